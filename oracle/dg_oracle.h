@@ -1,0 +1,99 @@
+/*
+ * dg_oracle.h -- plain, slow FP64 CPU restatement of the TENET modal DG
+ * method for the 3D Euler equations (Bauer et al., arXiv:1602.09079, Sect. 2).
+ *
+ * TEST INFRASTRUCTURE ONLY. This is the oracle that the CUDA path is checked
+ * against. Only tests/, __graft_entry__.smoke() and bench.py's cpu_baseline /
+ * reference arm may load it. It shares no code, header, table or constant
+ * with the CUDA library, and the CUDA library never calls it.
+ *
+ * Conventions (all written from the paper):
+ *   - k: polynomial degree (order O = k+1, Sect. 3), N(k) = (k+1)(k+2)(k+3)/6
+ *     modes per variable (Sect. 2.2).
+ *   - basis phi_l(xi) = Pt_u(xi1) Pt_v(xi2) Pt_w(xi3), u+v+w <= k, Pt_u the
+ *     Legendre polynomial scaled so that (1/8) int phi_l phi_m = delta_lm
+ *     (Sect. 2.2, orthonormal basis with w_0 = cell mean).
+ *   - mode order: total degree ascending, then u descending, then v
+ *     descending.
+ *   - state layout: [nz][ny][nx][5][N], variables (rho, rho vx, rho vy,
+ *     rho vz, E), cell (ix,iy,iz) centred at ((ix+1/2)dx, ...).
+ *   - R follows Eq. "dg:eqn:time": dw/dt + R(w) = 0.
+ */
+#ifndef DG_ORACLE_H
+#define DG_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  ORC_OK = 0,
+  ORC_ERR_ARG = -1,
+  ORC_ERR_NONFINITE = -4,
+  ORC_ERR_POSITIVITY = -5,
+  ORC_ERR_NEWTON = -6
+};
+
+typedef struct {
+  int k;              /* polynomial degree 0..3 */
+  int n[3];           /* cells per axis */
+  double L[3];        /* periodic box lengths, origin at 0 */
+  double gamma;       /* ideal-gas adiabatic index */
+  double eps_rho;     /* positivity floor for density */
+  double eps_p;       /* positivity floor for pressure */
+  int n_force;        /* number of forcing Fourier modes (0 = none) */
+  const int32_t* force_n;   /* 3*n_force integer wave vectors n, k = 2 pi n / L */
+  const double* force_a;    /* 6*n_force: Re a_x,a_y,a_z, Im a_x,a_y,a_z */
+} orc_params;
+
+int orc_nmodes(int k);
+void orc_mode_exponents(int k, int32_t* uvw /* 3*N */);
+void orc_gauss(int q, double* x, double* w);
+void orc_gll(int m, double* x, double* w);
+int orc_gll_count(int k);
+void orc_basis(int k, const double xi[3], double* phi, double* dphi /* 3*N, may be NULL */);
+
+/* volume Gauss points (physical coordinates), layout [cell][Q^3][3], point
+ * index q = a + Q*(b + Q*c) with a along x */
+int orc_volume_points(const orc_params* p, double* xyz);
+/* w = (1/8) sum_q f(x_q) phi_l(xi_q) omega_q, Sect. 2.3;
+ * f layout [cell][5][Q^3] */
+int orc_project(const orc_params* p, const double* f, double* w);
+/* evaluate the state polynomial of one cell at reference point xi */
+void orc_eval(const orc_params* p, const double* w, long cell, const double xi[3], double* U);
+
+void orc_euler_flux(int dir, double gamma, const double* U, double* F);
+void orc_hllc(int dir, double gamma, const double* UL, const double* UR, double* F);
+
+/* R(w) for all cells (Eqs. dg:eqn:volume_int, dg:eqn:surface_int) */
+int orc_rhs(const orc_params* p, const double* w, double* R);
+/* R(w) for a list of cells only; R layout [n_cells][5][N] */
+int orc_rhs_cells(const orc_params* p, const double* w, long n_cells, const int64_t* cells, double* R);
+
+/* forcing acceleration a(x) at physical points, xyz [n][3] -> a [n][3] */
+void orc_forcing_accel(const orc_params* p, long n, const double* xyz, double* a);
+
+/* Zhang-Shu positivity limiter, Sect. 2.5; flags [n_c] (may be NULL),
+ * per cell bit0 = theta1<1, bit1 = theta2<1 */
+int orc_limit(const orc_params* p, double* w, int8_t* flags, int64_t* n_limited);
+int orc_limit_cells(const orc_params* p, double* w, long n_cells, const int64_t* cells, int8_t* flags);
+/* tau solving P(qbar + tau (q - qbar)) = eps by Newton from tau = 1 */
+double orc_pressure_tau(double gamma, const double* qbar, const double* q, double eps, int* iters);
+
+/* time step by Eq. time_step_pos with the limited cell means */
+int orc_cfl_dt(const orc_params* p, const double* w, double courant, double* dt);
+/* one SSP-RK3 step (Shu-Osher form) with the limiter at each stage start */
+int orc_step(const orc_params* p, double* w, double dt);
+/* isothermal energy reset (Sect. 3.2) followed by the limiter */
+int orc_energy_reset(const orc_params* p, double* w, double c_iso, double rho0, double* dissipated);
+int orc_energy_reset_cells(const orc_params* p, double* w, long n_cells, const int64_t* cells,
+                           double c_iso, double rho0);
+/* sum_K |K| w_{i,0} */
+void orc_totals(const orc_params* p, const double* w, double* out5);
+int orc_num_threads(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
