@@ -1,0 +1,171 @@
+/*
+ * dg.h -- C ABI of the GB300 (sm_103a) modal discontinuous Galerkin solver
+ * for the 3D Euler equations on a periodic Cartesian mesh, following
+ * Bauer et al., "Simulating Turbulence Using the Astrophysical Discontinuous
+ * Galerkin Code TENET" (arXiv:1602.09079), Sect. 2 (method) and Sect. 3.1-3.2
+ * (driving and energy reset).
+ *
+ * Conventions
+ *   order     paper's convergence order O = k + 1 (Sect. 3), 1..4; k is the
+ *             polynomial degree, N(k) = (k+1)(k+2)(k+3)/6 modes (Sect. 2.2).
+ *   basis     phi_l = Pt_u(xi1) Pt_v(xi2) Pt_w(xi3), u+v+w <= k, with
+ *             Pt_u = sqrt(2u+1) P_u so that (1/8) int phi_l phi_m = delta_lm
+ *             and w_0 is the cell mean (Sect. 2.1-2.2). Mode order: total
+ *             degree ascending, then u descending, then v descending.
+ *   variables (rho, rho vx, rho vy, rho vz, E), ideal gas (Sect. 2.3).
+ *   canonical layout (exchange format, host or device):
+ *             [nz][ny][nx][5][N] doubles, cell (ix,iy,iz) centred at
+ *             ((ix+1/2) dx, (iy+1/2) dy, (iz+1/2) dz), box origin at 0.
+ *   state layout (the bound state buffer and dg_rhs operands):
+ *             [5][N][n_cells] doubles, cells x-fastest (mode-major,
+ *             cell-minor: every row is contiguous over cells).
+ *   R         right-hand side of Eq. dg:eqn:time, dw/dt + R(w) = 0.
+ *
+ * Memory: the library never allocates device memory. The caller allocates
+ * the state and one scratch buffer (sizes from dg_sizes), binds them with
+ * dg_bind, and owns them; they must stay valid while bound.
+ *
+ * Streams and errors: every call enqueues on the bound CUDA stream and
+ * returns without synchronising, except the calls that return host values
+ * (dg_cfl_dt, dg_totals, dg_limit with n_limited, dg_energy_reset with
+ * dissipated, dg_get_state to host, dg_check), which synchronise the stream.
+ * Conditions found on the device (non-finite values, a cell mean below the
+ * positivity floor, Newton non-convergence in the limiter) set a sticky
+ * device error word that the next synchronising call reports and clears.
+ * All functions return DG_OK (0) or a negative DG_ERR_* code and never
+ * throw across the ABI. Functions are not thread-safe on one context.
+ */
+#ifndef DG_GB300_H
+#define DG_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DG_OK 0
+#define DG_ERR_ARG -1          /* invalid argument or state */
+#define DG_ERR_NOT_BOUND -2    /* no state/scratch bound */
+#define DG_ERR_CUDA -3         /* a CUDA runtime call failed */
+#define DG_ERR_NONFINITE -4    /* NaN/Inf found in the state */
+#define DG_ERR_POSITIVITY -5   /* a cell mean density or pressure below eps */
+#define DG_ERR_NEWTON -6       /* limiter Newton iteration did not converge */
+
+#define DG_PREC_FP64 0   /* every step in FP64 */
+#define DG_PREC_MIXED 1  /* quadrature, fluxes and projection in FP32; RK
+                            accumulation, limiter, CFL and sums in FP64 */
+
+#define DG_FEATURE_FORCING 1  /* scratch sized for the driving field */
+
+typedef struct {
+  int32_t n[3];      /* cells per axis, each >= 1 */
+  double length[3];  /* periodic box lengths, each > 0 */
+} dg_mesh;
+
+typedef struct dg_ctx dg_ctx; /* opaque, owned by the library */
+
+/* Human-readable text of a status code (static storage). */
+const char* dg_strerror(int code);
+
+/* Create a context for a mesh, order O = k+1 in 1..4 (Sect. 3) and adiabatic
+ * index gamma > 1 (Sect. 2.3). Uploads the basis/quadrature tables to the
+ * current device. Positivity floors default to 1e-12, precision to FP64.
+ * Errors: DG_ERR_ARG for bad arguments, DG_ERR_CUDA. */
+int dg_init(const dg_mesh* mesh, int order, double gamma, dg_ctx** out);
+
+/* Destroy a context (does not free bound buffers). NULL is ignored. */
+void dg_destroy(dg_ctx* ctx);
+
+/* Sizes the caller must allocate: state_len doubles for the state
+ * (5 N n_cells) and scratch_bytes bytes of device scratch; features is a
+ * bit set of DG_FEATURE_*. */
+int dg_sizes(const dg_ctx* ctx, int features, size_t* state_len, size_t* scratch_bytes);
+
+/* Bind caller-owned device buffers and a CUDA stream (cudaStream_t, NULL =
+ * legacy default stream). y_dev: state layout, 5 N n_cells doubles, 8-byte
+ * aligned; scratch_dev: at least dg_sizes(ctx, 0, ...) bytes, 256-byte
+ * aligned; a scratch of dg_sizes(ctx, DG_FEATURE_FORCING, ...) bytes enables
+ * dg_set_forcing. Errors: DG_ERR_ARG (NULL, misaligned, too small). */
+int dg_bind(dg_ctx* ctx, double* y_dev, void* scratch_dev, size_t scratch_bytes, void* cuda_stream);
+
+/* Copy a canonical-layout state (host if is_device == 0, else device) into
+ * the bound state. Marks the state as not yet limited. */
+int dg_set_state(dg_ctx* ctx, const double* src, int is_device);
+
+/* Copy the bound state out in canonical layout (host or device). */
+int dg_get_state(dg_ctx* ctx, double* dst, int is_device);
+
+/* Physical coordinates of the volume Gauss points, written to host memory
+ * as [n_cells][Q^3][3] with Q = k+1 and point index a + Q (b + Q c)
+ * (a along x). These are the points at which dg_project expects values. */
+int dg_quadrature_points(const dg_ctx* ctx, double* xyz_host);
+
+/* Initial L2 projection (Sect. 2.3, w_l = 1/8 sum_q q(x_q) phi_l(xi_q)
+ * omega_q): q_points_dev holds conserved variables at the points of
+ * dg_quadrature_points, device memory, layout [n_cells][5][Q^3]. Writes the
+ * bound state (no limiting). */
+int dg_project(dg_ctx* ctx, const double* q_points_dev);
+
+/* R(y) of Eq. dg:eqn:time: volume integral (Eq. dg:eqn:volume_int) plus
+ * surface integral with the HLLC numerical flux (Eq. dg:eqn:surface_int),
+ * divided by |K| (Eq. dg:eqn:time_deriv, orthonormal basis), plus the
+ * driving source (Sect. 3.1) when set. y_dev and R_dev are device buffers in
+ * the state layout; y_dev == NULL means the bound state. No limiting. Uses
+ * the current precision mode; R is written in FP64. */
+int dg_rhs(dg_ctx* ctx, const double* y_dev, double* R_dev);
+
+/* One SSP-RK3 step (Sect. 2.4, Shu-Osher form) of size dt > 0 on the bound
+ * state, in place, with the positivity limiter (Sect. 2.5) applied to the
+ * state at the start of every stage; the state left behind is limited (it is
+ * the start of the next step's first stage). */
+int dg_step(dg_ctx* ctx, double dt);
+
+/* Positivity limiter (Sect. 2.5) on the bound state in place: theta1 from
+ * the density minimum over S = S_x u S_y u S_z (m GLL x (k+1)^2 Gauss points
+ * per direction), then theta2 from the pressure via Newton-Raphson for tau
+ * in P(qbar + tau (q - qbar)) = eps. flags_dev (nullable, device, n_cells
+ * int8): bit0 theta1 < 1, bit1 theta2 < 1. n_limited (nullable, host):
+ * number of limited cells; non-NULL synchronises. */
+int dg_limit(dg_ctx* ctx, int8_t* flags_dev, int64_t* n_limited);
+
+/* Global time step by Eq. time_step_pos: min over cells of
+ * C min(1/(2k+1), w1/2) / sum_a (|v_a| + c)/dx_a from the cell means, with
+ * w1 the first GLL weight. Synchronises; reports device errors. */
+int dg_cfl_dt(dg_ctx* ctx, double courant, double* dt_out);
+
+/* DG_PREC_FP64 or DG_PREC_MIXED. */
+int dg_set_precision(dg_ctx* ctx, int mode);
+
+/* Positivity floors for density and pressure (Sect. 2.5 "minimum target
+ * density"), both > 0. */
+int dg_set_eps(dg_ctx* ctx, double eps_rho, double eps_p);
+
+/* Driving acceleration a(x) = sum_j Re(ahat_j exp(i k_j . x)),
+ * k_j = 2 pi n_j / L (Sect. 3.1), added as the source (0, rho a, m . a) at
+ * the volume points of every stage. nvec_host: 3 n_modes int32 wave numbers;
+ * ahat_host: 6 n_modes doubles (Re a_x, a_y, a_z, Im a_x, a_y, a_z).
+ * n_modes = 0 switches the driving off. n_modes <= 256. Needs a scratch
+ * sized with DG_FEATURE_FORCING (else DG_ERR_ARG). */
+int dg_set_forcing(dg_ctx* ctx, int n_modes, const int32_t* nvec_host, const double* ahat_host);
+
+/* Isothermal energy reset (Sect. 3.2): at every volume point enforce
+ * eps = c^2/(gamma-1) (rho/rho0)^(gamma-1), re-project the energy weights
+ * from 1/2 |m|^2/rho + rho eps, then apply the positivity limiter.
+ * dissipated (nullable, host): sum over cells of |K| times the drop of the
+ * mean internal energy density; non-NULL synchronises. */
+int dg_energy_reset(dg_ctx* ctx, double c_iso, double rho0, double* dissipated);
+
+/* Conserved totals sum_K |K| w_{i,0}, i = 0..4, in FP64 (host out[5]).
+ * Synchronises. */
+int dg_totals(dg_ctx* ctx, double* out5);
+
+/* Synchronise the bound stream and report (and clear) the device error
+ * word. */
+int dg_check(dg_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

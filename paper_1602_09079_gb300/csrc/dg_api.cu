@@ -1,0 +1,687 @@
+// dg_api.cu -- the C ABI of include/dg.h: context, caller-owned buffer
+// binding, basis/quadrature tables (closed forms), layout transforms,
+// deterministic reductions, and the SSP-RK3 driver (arXiv:1602.09079,
+// Sect. 2.4) that sequences the per-degree kernels.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "dg.h"
+#include "dg_launch.h"
+
+using namespace dg;
+
+// ----------------------------------------------------------------- tables
+namespace {
+
+// Gauss-Legendre nodes (ascending) and weights on [-1,1], closed forms for
+// 1..4 points.
+void gauss_rule(int q, double* x, double* w) {
+  if (q == 1) {
+    x[0] = 0.0;
+    w[0] = 2.0;
+  } else if (q == 2) {
+    const double a = 1.0 / std::sqrt(3.0);
+    x[0] = -a; x[1] = a;
+    w[0] = w[1] = 1.0;
+  } else if (q == 3) {
+    const double a = std::sqrt(3.0 / 5.0);
+    x[0] = -a; x[1] = 0.0; x[2] = a;
+    w[0] = w[2] = 5.0 / 9.0;
+    w[1] = 8.0 / 9.0;
+  } else {
+    const double r = 2.0 / 7.0 * std::sqrt(6.0 / 5.0);
+    const double xi = std::sqrt(3.0 / 7.0 - r), xo = std::sqrt(3.0 / 7.0 + r);
+    const double wi = (18.0 + std::sqrt(30.0)) / 36.0, wo = (18.0 - std::sqrt(30.0)) / 36.0;
+    x[0] = -xo; x[1] = -xi; x[2] = xi; x[3] = xo;
+    w[0] = wo; w[1] = wi; w[2] = wi; w[3] = wo;
+  }
+}
+
+// Gauss-Lobatto-Legendre points: m = 2 {-1, 1}, m = 3 {-1, 0, 1}.
+void gll_rule(int m, double* x, double* w) {
+  if (m == 2) {
+    x[0] = -1.0; x[1] = 1.0;
+    w[0] = w[1] = 1.0;
+  } else {
+    x[0] = -1.0; x[1] = 0.0; x[2] = 1.0;
+    w[0] = w[2] = 1.0 / 3.0;
+    w[1] = 4.0 / 3.0;
+  }
+}
+
+// sqrt(2u+1) P_u(x) and its derivative, explicit polynomials for u <= 3.
+double pt(int u, double x) {
+  switch (u) {
+    case 0: return 1.0;
+    case 1: return std::sqrt(3.0) * x;
+    case 2: return std::sqrt(5.0) * 0.5 * (3.0 * x * x - 1.0);
+    default: return std::sqrt(7.0) * 0.5 * (5.0 * x * x * x - 3.0 * x);
+  }
+}
+double dpt(int u, double x) {
+  switch (u) {
+    case 0: return 0.0;
+    case 1: return std::sqrt(3.0);
+    case 2: return std::sqrt(5.0) * 3.0 * x;
+    default: return std::sqrt(7.0) * 0.5 * (15.0 * x * x - 3.0);
+  }
+}
+
+// Mode exponents in the exchange order: total degree ascending, then u
+// descending, then v descending.
+void modes(int k, int* e) {
+  int l = 0;
+  for (int d = 0; d <= k; ++d)
+    for (int u = d; u >= 0; --u)
+      for (int v = d - u; v >= 0; --v) {
+        e[3 * l] = u;
+        e[3 * l + 1] = v;
+        e[3 * l + 2] = d - u - v;
+        ++l;
+      }
+}
+
+void basis_at(int k, const double xi[3], double* phi, double* grad /*3N or null*/) {
+  int e[3 * 20];
+  modes(k, e);
+  const int N = nmodes(k);
+  for (int l = 0; l < N; ++l) {
+    const int u = e[3 * l], v = e[3 * l + 1], w = e[3 * l + 2];
+    const double a = pt(u, xi[0]), b = pt(v, xi[1]), c = pt(w, xi[2]);
+    phi[l] = a * b * c;
+    if (grad) {
+      grad[3 * l] = dpt(u, xi[0]) * b * c;
+      grad[3 * l + 1] = a * dpt(v, xi[1]) * c;
+      grad[3 * l + 2] = a * b * dpt(w, xi[2]);
+    }
+  }
+}
+
+template <int K>
+void build_tables(double* t) {
+  using TB = Tab<K>;
+  constexpr int Q = TB::Q, N = TB::N, Q2 = TB::Q2, M = TB::M;
+  double g[4], gw[4], h[3], hw[3];
+  gauss_rule(Q, g, gw);
+  gll_rule(M, h, hw);
+  std::memset(t, 0, sizeof(double) * TB::SIZE);
+  double phi[20], grad[60];
+  for (int c = 0; c < Q; ++c)
+    for (int b = 0; b < Q; ++b)
+      for (int a = 0; a < Q; ++a) {
+        const int q = a + Q * (b + Q * c);
+        const double xi[3] = {g[a], g[b], g[c]};
+        const double om = gw[a] * gw[b] * gw[c];
+        basis_at(K, xi, phi, grad);
+        for (int l = 0; l < N; ++l) {
+          t[TB::VPHI + q * N + l] = phi[l];
+          t[TB::VPHIW + q * N + l] = phi[l] * om / 8.0;
+          for (int d = 0; d < 3; ++d) t[TB::VDPHI + (d * TB::Q3 + q) * N + l] = grad[3 * l + d] * om / 4.0;
+        }
+      }
+  for (int d = 0; d < 3; ++d) {
+    const int o1 = d == 0 ? 1 : 0, o2 = d == 2 ? 1 : 2;  // the other two axes, ascending
+    for (int s = 0; s < 2; ++s)
+      for (int t2 = 0; t2 < Q; ++t2)
+        for (int t1 = 0; t1 < Q; ++t1) {
+          const int p = t1 + Q * t2;
+          double xi[3];
+          xi[d] = s ? 1.0 : -1.0;
+          xi[o1] = g[t1];
+          xi[o2] = g[t2];
+          basis_at(K, xi, phi, nullptr);
+          for (int l = 0; l < N; ++l) {
+            t[TB::FPHI + ((d * 2 + s) * Q2 + p) * N + l] = phi[l];
+            t[TB::FPHIW + ((d * 2 + s) * Q2 + p) * N + l] = phi[l] * gw[t1] * gw[t2] / 4.0;
+          }
+        }
+  }
+  int n = 0;
+  for (int d = 0; d < 3; ++d) {
+    const int o1 = d == 0 ? 1 : 0, o2 = d == 2 ? 1 : 2;
+    for (int r = 0; r < M; ++r)
+      for (int t2 = 0; t2 < Q; ++t2)
+        for (int t1 = 0; t1 < Q; ++t1) {
+          double xi[3];
+          xi[d] = h[r];
+          xi[o1] = g[t1];
+          xi[o2] = g[t2];
+          basis_at(K, xi, phi, nullptr);
+          for (int l = 0; l < N; ++l) {
+            t[TB::LPHI + n * N + l] = phi[l];
+            t[TB::LMAX + l] = std::fmax(t[TB::LMAX + l], std::fabs(phi[l]));
+          }
+          ++n;
+        }
+  }
+  for (int a = 0; a < Q; ++a) {
+    t[TB::GX + a] = g[a];
+    t[TB::GW + a] = gw[a];
+  }
+}
+
+Launchers launchers_for(int k) {
+  switch (k) {
+    case 0: return launchers_k0();
+    case 1: return launchers_k1();
+    case 2: return launchers_k2();
+    default: return launchers_k3();
+  }
+}
+
+std::mutex g_upload_mu;
+unsigned long long g_uploaded[4] = {0, 0, 0, 0};  // bit per device
+
+int upload_tables(int k, int dev) {
+  std::lock_guard<std::mutex> lock(g_upload_mu);
+  if (dev >= 0 && dev < 64 && (g_uploaded[k] >> dev) & 1ull) return DG_OK;
+  std::vector<double> t64(TAB_STRIDE, 0.0);
+  switch (k) {
+    case 0: build_tables<0>(t64.data()); break;
+    case 1: build_tables<1>(t64.data()); break;
+    case 2: build_tables<2>(t64.data()); break;
+    default: build_tables<3>(t64.data()); break;
+  }
+  std::vector<float> t32(TAB_STRIDE);
+  for (int i = 0; i < TAB_STRIDE; ++i) t32[i] = (float)t64[i];
+  Launchers L = launchers_for(k);
+  if (L.upload(t64.data(), t32.data()) != cudaSuccess) return DG_ERR_CUDA;
+  if (dev >= 0 && dev < 64) g_uploaded[k] |= 1ull << dev;
+  return DG_OK;
+}
+
+// ------------------------------------------------------ helper kernels
+// canonical [nc][R] <-> state [R][nc] (R = 5N), 32x32 tiles
+__global__ void canon_to_state_kernel(const double* __restrict__ in, double* __restrict__ out, long long nc, int R) {
+  __shared__ double tile[32][33];
+  const long long c0 = (long long)blockIdx.x * 32;
+  const int r0 = blockIdx.y * 32;
+  for (int j = threadIdx.y; j < 32; j += 8) {
+    const long long c = c0 + j;
+    const int r = r0 + threadIdx.x;
+    if (c < nc && r < R) tile[j][threadIdx.x] = in[(size_t)c * R + r];
+  }
+  __syncthreads();
+  for (int j = threadIdx.y; j < 32; j += 8) {
+    const int r = r0 + j;
+    const long long c = c0 + threadIdx.x;
+    if (c < nc && r < R) out[(size_t)r * nc + c] = tile[threadIdx.x][j];
+  }
+}
+
+__global__ void state_to_canon_kernel(const double* __restrict__ in, double* __restrict__ out, long long nc, int R) {
+  __shared__ double tile[32][33];
+  const long long c0 = (long long)blockIdx.x * 32;
+  const int r0 = blockIdx.y * 32;
+  for (int j = threadIdx.y; j < 32; j += 8) {
+    const int r = r0 + j;
+    const long long c = c0 + threadIdx.x;
+    if (c < nc && r < R) tile[j][threadIdx.x] = in[(size_t)r * nc + c];
+  }
+  __syncthreads();
+  for (int j = threadIdx.y; j < 32; j += 8) {
+    const long long c = c0 + j;
+    const int r = r0 + threadIdx.x;
+    if (c < nc && r < R) out[(size_t)c * R + r] = tile[threadIdx.x][j];
+  }
+}
+
+constexpr int kRedBlocks = 1024;
+
+// part[i * gridDim.x + b] = sum of the cell means of variable i over block b's
+// cells (fixed assignment and tree order: deterministic).
+__global__ void __launch_bounds__(256) means_partial_kernel(const double* __restrict__ y, long long nc, int N,
+                                                            double* __restrict__ part) {
+  __shared__ double s[256];
+  for (int i = 0; i < 5; ++i) {
+    double acc = 0.0;
+    for (long long c = (long long)blockIdx.x * 256 + threadIdx.x; c < nc; c += (long long)gridDim.x * 256)
+      acc += y[(size_t)i * N * nc + c];
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+      if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) part[i * gridDim.x + blockIdx.x] = s[0];
+    __syncthreads();
+  }
+}
+
+// out[j] = scale * sum_b part[j * n + b], one block per j, fixed order.
+__global__ void __launch_bounds__(256) sum_rows_kernel(const double* __restrict__ part, int n, double scale,
+                                                       double* __restrict__ out) {
+  __shared__ double s[256];
+  double acc = 0.0;
+  for (int b = threadIdx.x; b < n; b += 256) acc += part[(size_t)blockIdx.x * n + b];
+  s[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = s[0] * scale;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+constexpr int kMaxForce = 256;
+
+}  // namespace
+
+// ------------------------------------------------------------------ context
+struct dg_ctx {
+  int k = 1;
+  int N = 4, Q = 2;
+  int device = 0;
+  Geo geo{};
+  double L[3] = {1, 1, 1};
+  Launchers fn{};
+  // binding
+  bool bound = false;
+  double* y = nullptr;
+  unsigned char* scratch = nullptr;
+  size_t scratch_bytes = 0;
+  cudaStream_t stream = nullptr;
+  bool forcing_capable = false;
+  // scratch carve-up
+  Ctrl* ctrl = nullptr;
+  double* part = nullptr;
+  double* modes_dev = nullptr;
+  double* sums = nullptr;  // 8 doubles
+  double* ybuf = nullptr;
+  void* fh = nullptr;
+  void* field = nullptr;
+  // settings
+  int prec = DG_PREC_FP64;
+  bool limited = false;
+  int n_force = 0;
+  std::vector<double> modes_host;  // 9 per mode
+};
+
+namespace {
+
+struct Layout {
+  size_t ctrl, part, modes, sums, ybuf, fh, field, base_end, full_end;
+};
+
+Layout layout_of(const dg_ctx* c) {
+  Layout L{};
+  const size_t nc = (size_t)c->geo.nc;
+  size_t o = 0;
+  L.ctrl = o;
+  o += align256(sizeof(Ctrl));
+  L.part = o;
+  size_t npart = nc / 16 + 2 * kRedBlocks * 5 + 64;
+  o += align256(sizeof(double) * npart);
+  L.modes = o;
+  o += align256(sizeof(double) * 9 * kMaxForce);
+  L.sums = o;
+  o += align256(sizeof(double) * 8);
+  L.ybuf = o;
+  o += align256(sizeof(double) * 5 * c->N * nc);
+  L.fh = o;
+  o += align256(sizeof(double) * 15 * c->Q * c->Q * nc);
+  L.base_end = o;
+  L.field = o;
+  o += align256(sizeof(double) * 3 * c->Q * c->Q * c->Q * nc);
+  L.full_end = o;
+  return L;
+}
+
+int cuda_ok(cudaError_t e) { return e == cudaSuccess ? DG_OK : DG_ERR_CUDA; }
+
+#define DG_TRY(expr)                      \
+  do {                                    \
+    int _st = (expr);                     \
+    if (_st != DG_OK) return _st;         \
+  } while (0)
+#define DG_CUDA(expr) DG_TRY(cuda_ok(expr))
+
+int need_bound(const dg_ctx* c) {
+  if (!c) return DG_ERR_ARG;
+  return c->bound ? DG_OK : DG_ERR_NOT_BOUND;
+}
+
+int err_to_status(unsigned e) {
+  if (e & ERRB_NONFINITE) return DG_ERR_NONFINITE;
+  if (e & ERRB_POSITIVITY) return DG_ERR_POSITIVITY;
+  if (e & ERRB_NEWTON) return DG_ERR_NEWTON;
+  return DG_OK;
+}
+
+// Synchronise, read and clear the device error word.
+int sync_and_check(dg_ctx* c, Ctrl* host_copy) {
+  Ctrl h{};
+  DG_CUDA(cudaMemcpyAsync(&h, c->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream));
+  DG_CUDA(cudaStreamSynchronize(c->stream));
+  if (host_copy) *host_copy = h;
+  if (h.err) {
+    DG_CUDA(cudaMemsetAsync(&c->ctrl->err, 0, sizeof(unsigned), c->stream));
+    DG_CUDA(cudaStreamSynchronize(c->stream));
+  }
+  return err_to_status(h.err);
+}
+
+int set_device(const dg_ctx* c) { return cuda_ok(cudaSetDevice(c->device)); }
+
+int refresh_field(dg_ctx* c) {
+  if (c->n_force == 0) return DG_OK;
+  DG_CUDA(c->fn.forcing_field(c->prec, c->field, c->modes_dev, c->n_force, c->geo, c->L, c->stream));
+  return DG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* dg_strerror(int code) {
+  switch (code) {
+    case DG_OK: return "ok";
+    case DG_ERR_ARG: return "invalid argument";
+    case DG_ERR_NOT_BOUND: return "no state/scratch bound to the context";
+    case DG_ERR_CUDA: return "CUDA runtime error";
+    case DG_ERR_NONFINITE: return "non-finite value in the state";
+    case DG_ERR_POSITIVITY: return "cell mean density or pressure below the positivity floor";
+    case DG_ERR_NEWTON: return "positivity-limiter Newton iteration did not converge";
+    default: return "unknown status";
+  }
+}
+
+int dg_init(const dg_mesh* mesh, int order, double gamma, dg_ctx** out) {
+  if (!mesh || !out || order < 1 || order > 4 || !(gamma > 1.0) || !std::isfinite(gamma)) return DG_ERR_ARG;
+  long long nc = 1;
+  for (int a = 0; a < 3; ++a) {
+    if (mesh->n[a] < 1 || !(mesh->length[a] > 0.0) || !std::isfinite(mesh->length[a])) return DG_ERR_ARG;
+    nc *= mesh->n[a];
+  }
+  if (nc > (1LL << 31) - 1) return DG_ERR_ARG;
+  dg_ctx* c = new (std::nothrow) dg_ctx();
+  if (!c) return DG_ERR_ARG;
+  c->k = order - 1;
+  c->N = nmodes(c->k);
+  c->Q = c->k + 1;
+  if (cudaGetDevice(&c->device) != cudaSuccess) {
+    delete c;
+    return DG_ERR_CUDA;
+  }
+  c->geo.nx = mesh->n[0];
+  c->geo.ny = mesh->n[1];
+  c->geo.nz = mesh->n[2];
+  c->geo.nc = nc;
+  for (int a = 0; a < 3; ++a) {
+    c->L[a] = mesh->length[a];
+    c->geo.dx[a] = mesh->length[a] / mesh->n[a];
+    c->geo.inv_dx[a] = 1.0 / c->geo.dx[a];
+  }
+  c->geo.gamma = gamma;
+  c->geo.eps_rho = 1e-12;
+  c->geo.eps_p = 1e-12;
+  c->fn = launchers_for(c->k);
+  int st = upload_tables(c->k, c->device);
+  if (st != DG_OK) {
+    delete c;
+    return st;
+  }
+  *out = c;
+  return DG_OK;
+}
+
+void dg_destroy(dg_ctx* c) { delete c; }
+
+int dg_sizes(const dg_ctx* c, int features, size_t* state_len, size_t* scratch_bytes) {
+  if (!c) return DG_ERR_ARG;
+  Layout L = layout_of(c);
+  if (state_len) *state_len = (size_t)5 * c->N * (size_t)c->geo.nc;
+  if (scratch_bytes) *scratch_bytes = (features & DG_FEATURE_FORCING) ? L.full_end : L.base_end;
+  return DG_OK;
+}
+
+int dg_bind(dg_ctx* c, double* y_dev, void* scratch_dev, size_t scratch_bytes, void* cuda_stream) {
+  if (!c || !y_dev || !scratch_dev) return DG_ERR_ARG;
+  if (((uintptr_t)y_dev & 7u) || ((uintptr_t)scratch_dev & 255u)) return DG_ERR_ARG;
+  Layout L = layout_of(c);
+  if (scratch_bytes < L.base_end) return DG_ERR_ARG;
+  DG_TRY(set_device(c));
+  c->y = y_dev;
+  c->scratch = static_cast<unsigned char*>(scratch_dev);
+  c->scratch_bytes = scratch_bytes;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  c->forcing_capable = scratch_bytes >= L.full_end;
+  c->ctrl = reinterpret_cast<Ctrl*>(c->scratch + L.ctrl);
+  c->part = reinterpret_cast<double*>(c->scratch + L.part);
+  c->modes_dev = reinterpret_cast<double*>(c->scratch + L.modes);
+  c->sums = reinterpret_cast<double*>(c->scratch + L.sums);
+  c->ybuf = reinterpret_cast<double*>(c->scratch + L.ybuf);
+  c->fh = c->scratch + L.fh;
+  c->field = c->forcing_capable ? c->scratch + L.field : nullptr;
+  c->bound = true;
+  c->limited = false;
+  c->n_force = 0;
+  DG_CUDA(cudaMemsetAsync(c->ctrl, 0, sizeof(Ctrl), c->stream));
+  return DG_OK;
+}
+
+int dg_set_state(dg_ctx* c, const double* src, int is_device) {
+  DG_TRY(need_bound(c));
+  if (!src) return DG_ERR_ARG;
+  DG_TRY(set_device(c));
+  const int R = 5 * c->N;
+  const double* canon = src;
+  if (!is_device) {
+    DG_CUDA(cudaMemcpyAsync(c->ybuf, src, sizeof(double) * R * c->geo.nc, cudaMemcpyHostToDevice, c->stream));
+    canon = c->ybuf;
+  }
+  dim3 grid((unsigned)((c->geo.nc + 31) / 32), (R + 31) / 32);
+  canon_to_state_kernel<<<grid, dim3(32, 8), 0, c->stream>>>(canon, c->y, c->geo.nc, R);
+  DG_CUDA(cudaGetLastError());
+  c->limited = false;
+  return DG_OK;
+}
+
+int dg_get_state(dg_ctx* c, double* dst, int is_device) {
+  DG_TRY(need_bound(c));
+  if (!dst) return DG_ERR_ARG;
+  DG_TRY(set_device(c));
+  const int R = 5 * c->N;
+  double* canon = is_device ? dst : c->ybuf;
+  dim3 grid((unsigned)((c->geo.nc + 31) / 32), (R + 31) / 32);
+  state_to_canon_kernel<<<grid, dim3(32, 8), 0, c->stream>>>(c->y, canon, c->geo.nc, R);
+  DG_CUDA(cudaGetLastError());
+  if (!is_device) {
+    DG_CUDA(cudaMemcpyAsync(dst, c->ybuf, sizeof(double) * R * c->geo.nc, cudaMemcpyDeviceToHost, c->stream));
+    DG_CUDA(cudaStreamSynchronize(c->stream));
+  }
+  return DG_OK;
+}
+
+int dg_quadrature_points(const dg_ctx* c, double* xyz) {
+  if (!c || !xyz) return DG_ERR_ARG;
+  const int Q = c->Q;
+  double g[4], w[4];
+  gauss_rule(Q, g, w);
+  for (long long cell = 0; cell < c->geo.nc; ++cell) {
+    const int ix = (int)(cell % c->geo.nx), iy = (int)((cell / c->geo.nx) % c->geo.ny),
+              iz = (int)(cell / ((long long)c->geo.nx * c->geo.ny));
+    const int ijk[3] = {ix, iy, iz};
+    for (int cc = 0; cc < Q; ++cc)
+      for (int b = 0; b < Q; ++b)
+        for (int a = 0; a < Q; ++a) {
+          const int q = a + Q * (b + Q * cc);
+          const int ab[3] = {a, b, cc};
+          for (int d = 0; d < 3; ++d)
+            xyz[((size_t)cell * Q * Q * Q + q) * 3 + d] =
+                (ijk[d] + 0.5) * c->geo.dx[d] + 0.5 * c->geo.dx[d] * g[ab[d]];
+        }
+  }
+  return DG_OK;
+}
+
+int dg_project(dg_ctx* c, const double* q_points_dev) {
+  DG_TRY(need_bound(c));
+  if (!q_points_dev) return DG_ERR_ARG;
+  DG_TRY(set_device(c));
+  DG_CUDA(c->fn.project(q_points_dev, c->y, c->geo, c->stream));
+  c->limited = false;
+  return DG_OK;
+}
+
+int dg_rhs(dg_ctx* c, const double* y_dev, double* R_dev) {
+  DG_TRY(need_bound(c));
+  if (!R_dev) return DG_ERR_ARG;
+  DG_TRY(set_device(c));
+  const double* y = y_dev ? y_dev : c->y;
+  const bool force = c->n_force > 0;
+  DG_CUDA(c->fn.face(c->prec, y, c->fh, c->geo, c->stream));
+  DG_CUDA(c->fn.volume_rhs(c->prec, force, y, c->fh, c->field, c->geo, R_dev, c->ctrl, c->stream));
+  return DG_OK;
+}
+
+int dg_step(dg_ctx* c, double dt) {
+  DG_TRY(need_bound(c));
+  if (!(dt > 0.0) || !std::isfinite(dt)) return DG_ERR_ARG;
+  DG_TRY(set_device(c));
+  const bool force = c->n_force > 0;
+  if (!c->limited) DG_CUDA(c->fn.limit(c->y, nullptr, c->geo, c->ctrl, c->stream));
+  // Shu-Osher SSP-RK3: y1 = y0 - dt R(y0); y2 = 3/4 y0 + 1/4 (y1 - dt R(y1));
+  // y3 = 1/3 y0 + 2/3 (y2 - dt R(y2)); each output limited for the next stage.
+  const double a0[3] = {0.0, 0.75, 1.0 / 3.0};
+  const double b0[3] = {1.0, 0.25, 2.0 / 3.0};
+  const double* ys = c->y;
+  for (int s = 0; s < 3; ++s) {
+    double* out = s < 2 ? c->ybuf : c->y;
+    DG_CUDA(c->fn.face(c->prec, ys, c->fh, c->geo, c->stream));
+    DG_CUDA(c->fn.volume_stage(c->prec, force, c->fh, c->field, c->geo, ys, c->y, out, a0[s], b0[s], dt, c->ctrl,
+                               c->stream));
+    ys = out;
+  }
+  c->limited = true;
+  return DG_OK;
+}
+
+int dg_limit(dg_ctx* c, int8_t* flags_dev, int64_t* n_limited) {
+  DG_TRY(need_bound(c));
+  DG_TRY(set_device(c));
+  if (n_limited) DG_CUDA(cudaMemsetAsync(&c->ctrl->n_limited, 0, sizeof(unsigned long long), c->stream));
+  DG_CUDA(c->fn.limit(c->y, flags_dev, c->geo, c->ctrl, c->stream));
+  c->limited = true;
+  if (n_limited) {
+    Ctrl h{};
+    int st = sync_and_check(c, &h);
+    *n_limited = (int64_t)h.n_limited;
+    return st;
+  }
+  return DG_OK;
+}
+
+int dg_cfl_dt(dg_ctx* c, double courant, double* dt_out) {
+  DG_TRY(need_bound(c));
+  if (!dt_out || !(courant > 0.0)) return DG_ERR_ARG;
+  DG_TRY(set_device(c));
+  DG_CUDA(cudaMemsetAsync(&c->ctrl->cfl_max_bits, 0, sizeof(unsigned long long), c->stream));
+  DG_CUDA(c->fn.cfl(c->y, c->geo, c->ctrl, c->stream));
+  Ctrl h{};
+  int st = sync_and_check(c, &h);
+  if (st != DG_OK) return st;
+  double smax;
+  std::memcpy(&smax, &h.cfl_max_bits, sizeof(double));
+  if (!(smax > 0.0)) return DG_ERR_POSITIVITY;
+  // C min(1/(2k+1), w1/2) with w1 = 1 (m = 2 GLL points), 1/3 (m = 3)
+  const double w1 = gll_m(c->k) == 2 ? 1.0 : 1.0 / 3.0;
+  const double fac = std::fmin(1.0 / (2 * c->k + 1), w1 / 2.0);
+  *dt_out = courant * fac / smax;
+  return DG_OK;
+}
+
+int dg_set_precision(dg_ctx* c, int mode) {
+  if (!c || (mode != DG_PREC_FP64 && mode != DG_PREC_MIXED)) return DG_ERR_ARG;
+  const bool changed = c->prec != mode;
+  c->prec = mode;
+  if (changed && c->bound && c->n_force > 0) {
+    DG_TRY(set_device(c));
+    DG_TRY(refresh_field(c));
+  }
+  return DG_OK;
+}
+
+int dg_set_eps(dg_ctx* c, double eps_rho, double eps_p) {
+  if (!c || !(eps_rho > 0.0) || !(eps_p > 0.0) || !std::isfinite(eps_rho) || !std::isfinite(eps_p))
+    return DG_ERR_ARG;
+  c->geo.eps_rho = eps_rho;
+  c->geo.eps_p = eps_p;
+  c->limited = false;
+  return DG_OK;
+}
+
+int dg_set_forcing(dg_ctx* c, int n_modes, const int32_t* nvec, const double* ahat) {
+  DG_TRY(need_bound(c));
+  if (n_modes < 0 || n_modes > kMaxForce) return DG_ERR_ARG;
+  if (n_modes > 0 && (!nvec || !ahat || !c->forcing_capable)) return DG_ERR_ARG;
+  DG_TRY(set_device(c));
+  c->n_force = n_modes;
+  if (n_modes == 0) return DG_OK;
+  c->modes_host.assign((size_t)9 * n_modes, 0.0);
+  for (int j = 0; j < n_modes; ++j) {
+    for (int d = 0; d < 3; ++d) c->modes_host[9 * j + d] = (double)nvec[3 * j + d];
+    for (int d = 0; d < 6; ++d) {
+      if (!std::isfinite(ahat[6 * j + d])) {
+        c->n_force = 0;
+        return DG_ERR_ARG;
+      }
+      c->modes_host[9 * j + 3 + d] = ahat[6 * j + d];
+    }
+  }
+  DG_CUDA(cudaMemcpyAsync(c->modes_dev, c->modes_host.data(), sizeof(double) * 9 * n_modes, cudaMemcpyHostToDevice,
+                          c->stream));
+  DG_CUDA(cudaStreamSynchronize(c->stream));  // host copy may change on the next call
+  return refresh_field(c);
+}
+
+int dg_energy_reset(dg_ctx* c, double c_iso, double rho0, double* dissipated) {
+  DG_TRY(need_bound(c));
+  if (!(rho0 > 0.0) || !(c_iso >= 0.0) || !std::isfinite(c_iso) || !std::isfinite(rho0)) return DG_ERR_ARG;
+  DG_TRY(set_device(c));
+  int n_part = 0;
+  const double c2g = c_iso * c_iso / (c->geo.gamma - 1.0);
+  DG_CUDA(c->fn.energy_reset(c->prec, c->y, c->geo, c2g, 1.0 / rho0, c->part, &n_part, c->ctrl, c->stream));
+  c->limited = true;
+  if (dissipated) {
+    const double vol = c->geo.dx[0] * c->geo.dx[1] * c->geo.dx[2];
+    sum_rows_kernel<<<1, 256, 0, c->stream>>>(c->part, n_part, vol, c->sums);
+    DG_CUDA(cudaGetLastError());
+    double h = 0.0;
+    DG_CUDA(cudaMemcpyAsync(&h, c->sums, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    int st = sync_and_check(c, nullptr);
+    *dissipated = h;
+    return st;
+  }
+  return DG_OK;
+}
+
+int dg_totals(dg_ctx* c, double* out5) {
+  DG_TRY(need_bound(c));
+  if (!out5) return DG_ERR_ARG;
+  DG_TRY(set_device(c));
+  long long nb = (c->geo.nc + 255) / 256;
+  const int G = (int)(nb < kRedBlocks ? nb : kRedBlocks);
+  means_partial_kernel<<<G, 256, 0, c->stream>>>(c->y, c->geo.nc, c->N, c->part);
+  DG_CUDA(cudaGetLastError());
+  const double vol = c->geo.dx[0] * c->geo.dx[1] * c->geo.dx[2];
+  sum_rows_kernel<<<5, 256, 0, c->stream>>>(c->part, G, vol, c->sums);
+  DG_CUDA(cudaGetLastError());
+  DG_CUDA(cudaMemcpyAsync(out5, c->sums, sizeof(double) * 5, cudaMemcpyDeviceToHost, c->stream));
+  return sync_and_check(c, nullptr);
+}
+
+int dg_check(dg_ctx* c) {
+  DG_TRY(need_bound(c));
+  DG_TRY(set_device(c));
+  return sync_and_check(c, nullptr);
+}
+
+}  // extern "C"

@@ -1,0 +1,281 @@
+// dg_common.cuh -- shared device definitions of the GB300 modal DG solver
+// (arXiv:1602.09079, Sect. 2): table layout, ideal-gas physics, HLLC flux,
+// positivity limiter, launch geometry.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dg {
+
+// ------------------------------------------------------------- sizes
+__host__ __device__ constexpr int nmodes(int k) { return (k + 1) * (k + 2) * (k + 3) / 6; }
+__host__ __device__ constexpr int gll_m(int k) { return k <= 1 ? 2 : 3; }
+
+// Per-degree basis/quadrature tables (Sect. 2.2-2.5), all values at the
+// method's point sets, offsets in elements. Weights are folded in so the
+// kernels only multiply and add.
+template <int K>
+struct Tab {
+  static constexpr int Q = K + 1;
+  static constexpr int Q2 = Q * Q;
+  static constexpr int Q3 = Q * Q * Q;
+  static constexpr int N = nmodes(K);
+  static constexpr int M = gll_m(K);
+  static constexpr int NL = 3 * M * Q2;  // positivity point set S
+  // phi_l(xi_q) at volume Gauss points, [Q3][N]
+  static constexpr int VPHI = 0;
+  // dphi_l/dxi_a (xi_q) * omega_q / 4, [3][Q3][N]
+  static constexpr int VDPHI = VPHI + Q3 * N;
+  // phi_l(xi_q) * omega_q / 8, [Q3][N]
+  static constexpr int VPHIW = VDPHI + 3 * Q3 * N;
+  // phi_l at face points of face (a, s), s = 0 low (xi_a = -1) / 1 high, [3][2][Q2][N]
+  static constexpr int FPHI = VPHIW + Q3 * N;
+  // same times omega_2D / 4, [3][2][Q2][N]
+  static constexpr int FPHIW = FPHI + 6 * Q2 * N;
+  // phi_l at the limiter points, [NL][N]
+  static constexpr int LPHI = FPHIW + 6 * Q2 * N;
+  // max over S of |phi_l|, [N]
+  static constexpr int LMAX = LPHI + NL * N;
+  // 1D Gauss nodes and weights, [Q] each
+  static constexpr int GX = LMAX + N;
+  static constexpr int GW = GX + Q;
+  static constexpr int SIZE = GW + Q;
+};
+constexpr int TAB_STRIDE = 16384;  // >= Tab<3>::SIZE
+static_assert(Tab<3>::SIZE <= TAB_STRIDE, "table stride");
+
+// ------------------------------------------------------------ error word
+enum : unsigned {
+  ERRB_NONFINITE = 1u,
+  ERRB_POSITIVITY = 2u,
+  ERRB_NEWTON = 4u,
+};
+
+// Control block at the start of the scratch buffer.
+struct Ctrl {
+  unsigned long long cfl_max_bits;  // max over cells of the wave-speed sum (bits of a double >= 0)
+  unsigned int err;                 // sticky ERRB_* bits
+  unsigned int pad0;
+  unsigned long long n_limited;     // limiter count
+  double pad1[5];
+};
+
+struct Geo {
+  int nx, ny, nz;
+  long long nc;  // cells
+  double dx[3];
+  double inv_dx[3];
+  double gamma;
+  double eps_rho, eps_p;
+};
+
+// --------------------------------------------------------------- physics
+template <typename T>
+__device__ __forceinline__ T pressure_of(const T* U, T gm1) {
+  T ke = T(0.5) * (U[1] * U[1] + U[2] * U[2] + U[3] * U[3]) / U[0];
+  return gm1 * (U[4] - ke);
+}
+
+// Euler flux along direction d from conserved U, given velocity and pressure.
+template <typename T>
+__device__ __forceinline__ void euler_flux(int d, const T* U, const T* v, T p, T* F) {
+  T mn = U[1 + d];
+  F[0] = mn;
+  F[1] = mn * v[0];
+  F[2] = mn * v[1];
+  F[3] = mn * v[2];
+  F[1 + d] += p;
+  F[4] = (U[4] + p) * v[d];
+}
+
+// HLLC numerical flux across a face with normal +e_d, left = lower cell
+// (Sect. 2.3, "approximative HLLC Riemann solver"): Einfeldt wave-speed
+// estimates from Roe averages, middle wave and star states from the
+// Rankine-Hugoniot conditions across the three waves (Toro's formulation).
+template <typename T>
+__device__ __forceinline__ void hllc_flux(int d, const T* UL, const T* UR, T gamma, T* F) {
+  const T gm1 = gamma - T(1);
+  T irL = T(1) / UL[0], irR = T(1) / UR[0];
+  T vL[3] = {UL[1] * irL, UL[2] * irL, UL[3] * irL};
+  T vR[3] = {UR[1] * irR, UR[2] * irR, UR[3] * irR};
+  T pL = gm1 * (UL[4] - T(0.5) * UL[0] * (vL[0] * vL[0] + vL[1] * vL[1] + vL[2] * vL[2]));
+  T pR = gm1 * (UR[4] - T(0.5) * UR[0] * (vR[0] * vR[0] + vR[1] * vR[1] + vR[2] * vR[2]));
+  T cL = sqrt(gamma * pL * irL), cR = sqrt(gamma * pR * irR);
+  T sL = sqrt(UL[0]), sR = sqrt(UR[0]);
+  T iss = T(1) / (sL + sR);
+  T vt[3], v2 = T(0);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    vt[a] = (sL * vL[a] + sR * vR[a]) * iss;
+    v2 += vt[a] * vt[a];
+  }
+  T Ht = (sL * (UL[4] + pL) * irL + sR * (UR[4] + pR) * irR) * iss;
+  T c2t = gm1 * (Ht - T(0.5) * v2);
+  T ct = c2t > T(0) ? sqrt(c2t) : T(0);
+  T uL = vL[d], uR = vR[d];
+  T SL = fmin(uL - cL, vt[d] - ct);
+  T SR = fmax(uR + cR, vt[d] + ct);
+  if (SL >= T(0)) {
+    euler_flux(d, UL, vL, pL, F);
+    return;
+  }
+  if (SR <= T(0)) {
+    euler_flux(d, UR, vR, pR, F);
+    return;
+  }
+  T aL = UL[0] * (SL - uL), aR = UR[0] * (SR - uR);
+  T Ss = (pR - pL + uL * aL - uR * aR) / (aL - aR);
+  const bool left = Ss >= T(0);
+  const T* U = left ? UL : UR;
+  const T* v = left ? vL : vR;
+  T p = left ? pL : pR;
+  T S = left ? SL : SR;
+  T ak = left ? aL : aR;  // rho_K (S_K - u_K)
+  T uk = v[d];
+  euler_flux(d, U, v, p, F);
+  T chi = ak / (S - Ss);
+  T Us[5];
+  Us[0] = chi;
+  Us[1] = chi * v[0];
+  Us[2] = chi * v[1];
+  Us[3] = chi * v[2];
+  Us[1 + d] = chi * Ss;
+  Us[4] = chi * (U[4] / U[0] + (Ss - uk) * (Ss + p / ak));
+#pragma unroll
+  for (int i = 0; i < 5; ++i) F[i] += S * (Us[i] - U[i]);
+}
+
+// --------------------------------------------------------------- limiter
+// tau in [0,1] with P(qbar + tau (q - qbar)) = eps: Newton from tau = 1.
+// The pressure is concave along the segment, so the iterates decrease
+// monotonically; stop when a step is below 1e-15 (50 iterations at most).
+__device__ __forceinline__ double positivity_tau(const double* qb, const double* q, double gm1,
+                                                 double eps, int* iters) {
+  double d[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) d[i] = q[i] - qb[i];
+  double tau = 1.0;
+  int it = 0;
+  while (it < 50) {
+    double s0 = qb[0] + tau * d[0];
+    double s1 = qb[1] + tau * d[1];
+    double s2 = qb[2] + tau * d[2];
+    double s3 = qb[3] + tau * d[3];
+    double s4 = qb[4] + tau * d[4];
+    double m2 = s1 * s1 + s2 * s2 + s3 * s3;
+    double ir = 1.0 / s0;
+    double f = gm1 * (s4 - 0.5 * m2 * ir) - eps;
+    double md = s1 * d[1] + s2 * d[2] + s3 * d[3];
+    double fp = gm1 * (d[4] - md * ir + 0.5 * m2 * d[0] * ir * ir);
+    double tn = tau - f / fp;
+    if (!(tn >= 0.0)) tn = 0.0;
+    if (tn > tau) tn = tau;
+    double step = tau - tn;
+    tau = tn;
+    ++it;
+    if (step <= 1e-15) break;
+  }
+  *iters = it;
+  return tau;
+}
+
+// Zhang-Shu positivity limiter of one cell (Sect. 2.5) on its 5N FP64
+// coefficients w[(i*N + l) * stride]. A cheap sufficient test (mean minus
+// the sum of |w_l| max_S |phi_l|, with a rounding margin) skips the point
+// evaluations when the limiter provably leaves the cell unchanged.
+// Returns flag bits (1: theta1 < 1, 2: theta2 < 1) and ORs errors into err.
+template <int K>
+__device__ int limit_cell(double* w, long long stride, const double* __restrict__ tab, double gamma,
+                          double eps_r, double eps_p, unsigned* err) {
+  using TB = Tab<K>;
+  constexpr int N = TB::N;
+  const double gm1 = gamma - 1.0;
+  double mean[5];
+  bool finite = true;
+#pragma unroll
+  for (int i = 0; i < 5; ++i) mean[i] = w[(i * N) * stride];
+  for (int j = 0; j < 5 * N; ++j) finite &= isfinite(w[j * stride]);
+  if (!finite) {
+    *err |= ERRB_NONFINITE;
+    return 0;
+  }
+  double pbar = gm1 * (mean[4] - 0.5 * (mean[1] * mean[1] + mean[2] * mean[2] + mean[3] * mean[3]) / mean[0]);
+  if (!(mean[0] >= eps_r) || !(pbar >= eps_p)) {
+    *err |= ERRB_POSITIVITY;
+    return 0;
+  }
+  if (N == 1) return 0;
+  const double* lmax = tab + TB::LMAX;
+  const double* lphi = tab + TB::LPHI;
+  double sabs[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    double s = 0.0;
+    for (int l = 1; l < N; ++l) s += fabs(w[(i * N + l) * stride]) * __ldg(lmax + l);
+    sabs[i] = s;
+  }
+  int flag = 0;
+  // density: theta1
+  double rlo = mean[0] - sabs[0];
+  bool rho_safe = rlo >= eps_r + 1e-13 * (fabs(mean[0]) + sabs[0]);
+  if (!rho_safe) {
+    double rmin = mean[0];
+    for (int s = 0; s < TB::NL; ++s) {
+      double r = 0.0;
+#pragma unroll
+      for (int l = 0; l < N; ++l) r += w[l * stride] * __ldg(lphi + s * N + l);
+      rmin = fmin(rmin, r);
+    }
+    if (rmin < eps_r) {
+      double th1 = fmin(fabs((mean[0] - eps_r) / (mean[0] - rmin)), 1.0);
+      if (th1 < 1.0) {
+        for (int l = 1; l < N; ++l) w[l * stride] *= th1;
+        flag |= 1;
+      }
+    }
+  }
+  // pressure: theta2
+  bool p_safe = false;
+  if (rho_safe) {
+    double elo = mean[4] - sabs[4];
+    double kin = 0.0;
+#pragma unroll
+    for (int a = 1; a <= 3; ++a) {
+      double mh = fabs(mean[a]) + sabs[a];
+      kin += mh * mh;
+    }
+    kin *= 0.5 / rlo;
+    double plo = gm1 * (elo - kin);
+    p_safe = plo >= eps_p + 1e-13 * gm1 * (fabs(mean[4]) + sabs[4] + kin);
+  }
+  if (!p_safe) {
+    double th2 = 1.0;
+    bool newton_fail = false;
+    for (int s = 0; s < TB::NL; ++s) {
+      double U[5];
+#pragma unroll
+      for (int i = 0; i < 5; ++i) {
+        double acc = 0.0;
+#pragma unroll
+        for (int l = 0; l < N; ++l) acc += w[(i * N + l) * stride] * __ldg(lphi + s * N + l);
+        U[i] = acc;
+      }
+      double p = gm1 * (U[4] - 0.5 * (U[1] * U[1] + U[2] * U[2] + U[3] * U[3]) / U[0]);
+      if (p < eps_p) {
+        int it;
+        double tau = positivity_tau(mean, U, gm1, eps_p, &it);
+        if (it >= 50) newton_fail = true;
+        th2 = fmin(th2, tau);
+      }
+    }
+    if (newton_fail) *err |= ERRB_NEWTON;
+    if (th2 < 1.0) {
+      for (int i = 0; i < 5; ++i)
+        for (int l = 1; l < N; ++l) w[(i * N + l) * stride] *= th2;
+      flag |= 2;
+    }
+  }
+  return flag;
+}
+
+}  // namespace dg

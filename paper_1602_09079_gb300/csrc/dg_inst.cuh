@@ -1,0 +1,177 @@
+// dg_inst.cuh -- instantiates the kernels and launchers for one polynomial
+// degree DG_K (included by dg_k<K>.cu with DG_K defined).
+#pragma once
+#include "dg_kernels.cuh"
+#include "dg_launch.h"
+
+#ifndef DG_K
+#error "define DG_K before including dg_inst.cuh"
+#endif
+
+namespace dg {
+namespace {
+
+constexpr int KK = DG_K;
+using TB = Tab<KK>;
+
+// Degree-KK basis/quadrature tables in device memory, FP64 and FP32 copies.
+// Every device that loads the library holds its own copy; the host keeps
+// each device's symbol address.
+__device__ double g_tab64[TAB_STRIDE];
+__device__ float g_tab32[TAB_STRIDE];
+constexpr int kMaxDev = 64;
+const double* h_tab64[kMaxDev] = {};
+const float* h_tab32[kMaxDev] = {};
+
+inline int cur_dev() {
+  int d = 0;
+  cudaGetDevice(&d);
+  return d < kMaxDev ? d : 0;
+}
+
+template <typename T>
+const T* tab_ptr();
+template <>
+const double* tab_ptr<double>() { return h_tab64[cur_dev()]; }
+template <>
+const float* tab_ptr<float>() { return h_tab32[cur_dev()]; }
+
+inline unsigned grid1(long long n, int per) { return (unsigned)((n + per - 1) / per); }
+
+template <typename T, int MODE, bool FORCE>
+cudaError_t set_volume_smem() {
+  return cudaFuncSetAttribute(volume_kernel<KK, T, MODE, FORCE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)VolCfg<KK, T>::smem(FORCE));
+}
+
+cudaError_t upload(const double* h64, const float* h32) {
+  cudaError_t e = cudaMemcpyToSymbol(g_tab64, h64, sizeof(double) * TB::SIZE);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyToSymbol(g_tab32, h32, sizeof(float) * TB::SIZE);
+  if (e != cudaSuccess) return e;
+  void* p = nullptr;
+  const int dev = cur_dev();
+  if ((e = cudaGetSymbolAddress(&p, g_tab64)) != cudaSuccess) return e;
+  h_tab64[dev] = static_cast<const double*>(p);
+  if ((e = cudaGetSymbolAddress(&p, g_tab32)) != cudaSuccess) return e;
+  h_tab32[dev] = static_cast<const float*>(p);
+  cudaError_t r = cudaSuccess;
+  cudaError_t s[8] = {set_volume_smem<double, MODE_RHS, false>(),  set_volume_smem<double, MODE_RHS, true>(),
+                      set_volume_smem<double, MODE_STAGE, false>(), set_volume_smem<double, MODE_STAGE, true>(),
+                      set_volume_smem<float, MODE_RHS, false>(),   set_volume_smem<float, MODE_RHS, true>(),
+                      set_volume_smem<float, MODE_STAGE, false>(),  set_volume_smem<float, MODE_STAGE, true>()};
+  for (cudaError_t x : s)
+    if (x != cudaSuccess) r = x;
+  return r;
+}
+
+template <typename T>
+cudaError_t face_t(const double* y, void* fh, const Geo& g, cudaStream_t s) {
+  dim3 grid(grid1(g.nc, kThreads), TB::Q2, 3);
+  face_flux_kernel<KK, T><<<grid, kThreads, 0, s>>>(y, static_cast<T*>(fh), tab_ptr<T>(), g);
+  return cudaGetLastError();
+}
+
+cudaError_t face(int prec, const double* y, void* fh, const Geo& g, cudaStream_t s) {
+  return prec ? face_t<float>(y, fh, g, s) : face_t<double>(y, fh, g, s);
+}
+
+template <typename T, int MODE, bool FORCE>
+cudaError_t vol_t(const double* y, const void* fh, const void* field, const Geo& g, StageArgs st, double* R,
+                  Ctrl* ctrl, cudaStream_t s) {
+  using CF = VolCfg<KK, T>;
+  volume_kernel<KK, T, MODE, FORCE><<<grid1(g.nc, CF::C), kThreads, CF::smem(FORCE), s>>>(
+      y, static_cast<const T*>(fh), static_cast<const T*>(field), tab_ptr<T>(), tab_ptr<double>(), g, st, R, ctrl);
+  return cudaGetLastError();
+}
+
+cudaError_t volume_rhs(int prec, bool force, const double* y, const void* fh, const void* field, const Geo& g,
+                       double* R, Ctrl* ctrl, cudaStream_t s) {
+  StageArgs st{};
+  if (prec)
+    return force ? vol_t<float, MODE_RHS, true>(y, fh, field, g, st, R, ctrl, s)
+                 : vol_t<float, MODE_RHS, false>(y, fh, field, g, st, R, ctrl, s);
+  return force ? vol_t<double, MODE_RHS, true>(y, fh, field, g, st, R, ctrl, s)
+               : vol_t<double, MODE_RHS, false>(y, fh, field, g, st, R, ctrl, s);
+}
+
+cudaError_t volume_stage(int prec, bool force, const void* fh, const void* field, const Geo& g, const double* ys,
+                         const double* y0, double* out, double a0, double b0, double dt, Ctrl* ctrl,
+                         cudaStream_t s) {
+  StageArgs st{ys, y0, out, a0, b0, dt};
+  if (prec)
+    return force ? vol_t<float, MODE_STAGE, true>(ys, fh, field, g, st, nullptr, ctrl, s)
+                 : vol_t<float, MODE_STAGE, false>(ys, fh, field, g, st, nullptr, ctrl, s);
+  return force ? vol_t<double, MODE_STAGE, true>(ys, fh, field, g, st, nullptr, ctrl, s)
+               : vol_t<double, MODE_STAGE, false>(ys, fh, field, g, st, nullptr, ctrl, s);
+}
+
+cudaError_t limit(double* y, int8_t* flags, const Geo& g, Ctrl* ctrl, cudaStream_t s) {
+  limit_kernel<KK><<<grid1(g.nc, kThreads), kThreads, 0, s>>>(y, flags, tab_ptr<double>(), g, ctrl);
+  return cudaGetLastError();
+}
+
+cudaError_t cfl(const double* y, const Geo& g, Ctrl* ctrl, cudaStream_t s) {
+  unsigned nb = grid1(g.nc, kThreads);
+  if (nb > 152u * 8u) nb = 152u * 8u;
+  cfl_kernel<KK><<<nb, kThreads, 0, s>>>(y, g, ctrl);
+  return cudaGetLastError();
+}
+
+constexpr int kResetCells = KK >= 3 ? 16 : 32;
+
+template <typename T>
+cudaError_t reset_t(double* y, const Geo& g, double c2g, double inv_rho0, double* part, int* n_part, Ctrl* ctrl,
+                    cudaStream_t s) {
+  unsigned nb = grid1(g.nc, kResetCells);
+  *n_part = (int)nb;
+  energy_reset_kernel<KK, T, kResetCells><<<nb, kThreads, 0, s>>>(y, tab_ptr<T>(), tab_ptr<double>(), g, c2g, inv_rho0, part,
+                                                                  ctrl);
+  return cudaGetLastError();
+}
+
+cudaError_t energy_reset(int prec, double* y, const Geo& g, double c2g, double inv_rho0, double* part, int* n_part,
+                         Ctrl* ctrl, cudaStream_t s) {
+  return prec ? reset_t<float>(y, g, c2g, inv_rho0, part, n_part, ctrl, s)
+              : reset_t<double>(y, g, c2g, inv_rho0, part, n_part, ctrl, s);
+}
+
+cudaError_t project(const double* f, double* y, const Geo& g, cudaStream_t s) {
+  project_kernel<KK><<<grid1(5 * g.nc, kThreads), kThreads, 0, s>>>(f, y, tab_ptr<double>(), g);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t field_t(void* field, const double* modes, int n, const Geo& g, const double* L, cudaStream_t s) {
+  dim3 grid(grid1(g.nc, kThreads), TB::Q3);
+  forcing_field_kernel<KK, T><<<grid, kThreads, 0, s>>>(static_cast<T*>(field), modes, n, tab_ptr<double>(), g, L[0], L[1],
+                                                       L[2]);
+  return cudaGetLastError();
+}
+
+cudaError_t forcing_field(int prec, void* field, const double* modes, int n, const Geo& g, const double* L,
+                          cudaStream_t s) {
+  return prec ? field_t<float>(field, modes, n, g, L, s) : field_t<double>(field, modes, n, g, L, s);
+}
+
+}  // namespace
+
+#define DG_PASTE2(a, b) a##b
+#define DG_PASTE(a, b) DG_PASTE2(a, b)
+Launchers DG_PASTE(launchers_k, DG_K)() {
+  Launchers L;
+  L.k = KK;
+  L.upload = upload;
+  L.face = face;
+  L.volume_rhs = volume_rhs;
+  L.volume_stage = volume_stage;
+  L.limit = limit;
+  L.cfl = cfl;
+  L.energy_reset = energy_reset;
+  L.project = project;
+  L.forcing_field = forcing_field;
+  L.table_size = TB::SIZE;
+  return L;
+}
+
+}  // namespace dg

@@ -1,0 +1,3 @@
+// Kernels and launchers of the degree-2 modal DG basis (order 3).
+#define DG_K 2
+#include "dg_inst.cuh"

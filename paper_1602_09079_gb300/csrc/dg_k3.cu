@@ -1,0 +1,3 @@
+// Kernels and launchers of the degree-3 modal DG basis (order 4).
+#define DG_K 3
+#include "dg_inst.cuh"

@@ -1,0 +1,42 @@
+// dg_launch.h -- host-side launch interface between the C ABI (dg_api.cu)
+// and the per-degree kernel translation units (dg_k0.cu .. dg_k3.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dg_common.cuh"
+
+namespace dg {
+
+struct StageArgs;
+
+struct Launchers {
+  int k;
+  // copy the degree's tables (FP64 and FP32 copies) to the current device
+  cudaError_t (*upload)(const double* h64, const float* h32);
+  // one HLLC flux per face point; fh holds T = double (prec 0) or float (prec 1)
+  cudaError_t (*face)(int prec, const double* y, void* fh, const Geo& g, cudaStream_t s);
+  // R(y) written in FP64, state layout
+  cudaError_t (*volume_rhs)(int prec, bool force, const double* y, const void* fh, const void* field,
+                            const Geo& g, double* R, Ctrl* ctrl, cudaStream_t s);
+  // SSP-RK3 stage combination + limiter
+  cudaError_t (*volume_stage)(int prec, bool force, const void* fh, const void* field, const Geo& g,
+                              const double* ys, const double* y0, double* out, double a0, double b0,
+                              double dt, Ctrl* ctrl, cudaStream_t s);
+  cudaError_t (*limit)(double* y, int8_t* flags, const Geo& g, Ctrl* ctrl, cudaStream_t s);
+  cudaError_t (*cfl)(const double* y, const Geo& g, Ctrl* ctrl, cudaStream_t s);
+  // returns the number of partial sums written to part
+  cudaError_t (*energy_reset)(int prec, double* y, const Geo& g, double c2g, double inv_rho0, double* part,
+                              int* n_part, Ctrl* ctrl, cudaStream_t s);
+  cudaError_t (*project)(const double* f, double* y, const Geo& g, cudaStream_t s);
+  cudaError_t (*forcing_field)(int prec, void* field, const double* modes, int n_modes, const Geo& g,
+                               const double* L, cudaStream_t s);
+  size_t table_size;
+};
+
+Launchers launchers_k0();
+Launchers launchers_k1();
+Launchers launchers_k2();
+Launchers launchers_k3();
+
+}  // namespace dg
