@@ -1,0 +1,467 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 modal DG solver (arXiv:1602.09079).
+
+Workload (one "step" = one SSP-RK3 step of the whole hot path): driven
+subsonic turbulence on a periodic 128^3 box, order 3 (degree 2, 10 modes
+per variable), gamma = 5/3, warm start rho = 1, p = 1/gamma with a
+solenoidal velocity field at rms Mach 0.3 on the driving modes (seed 1234),
+OU-driven solenoidal forcing on 1 <= |n| <= 2 (seed 1234), CFL 0.3. Each
+step: CFL reduction (dg_cfl_dt), three fused stages (face fluxes, volume
+quadrature + projection + stage combination + positivity limiter), and the
+isothermal energy reset (dg_energy_reset).
+
+Metric: DOF-updates per second per RK stage = cells x N(k) x 3 stages x
+steps / time. The headline value is the FP32-mixed path (FP64 state, RK
+accumulation, limiter and reductions); the plain FP64 path is reported
+beside it with the mixed path's L2 error against it.
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of cells of the same workload (the oracle is the baseline here).
+Multi-GPU (torchrun): independent replicas, one per rank; value = all
+ranks' DOF-updates / max time over ranks.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synthetic as syn  # noqa: E402
+
+GAMMA = 5.0 / 3.0
+MACH = 0.3
+SEED = 1234
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=128, help="cells per axis")
+    ap.add_argument("--order", type=int, default=3)
+    ap.add_argument("--courant", type=float, default=0.3)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--err-steps", type=int, default=10)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--precisions", default="fp64,mixed",
+                    help="comma list of fp64,mixed (the first listed of mixed/fp64 is the headline)")
+    return ap.parse_args()
+
+
+def workload_config(args, precision):
+    n = args.n
+    N = (args.order) * (args.order + 1) * (args.order + 2) // 6
+    return {
+        "workload": (f"driven subsonic turbulence, periodic {n}^3 box, order {args.order} "
+                     f"(degree {args.order - 1}), gamma 5/3, warm start rms Mach {MACH} "
+                     f"(seed {SEED}), OU solenoidal forcing on 1<=|n|<=2, energy reset every "
+                     f"step, CFL {args.courant}"),
+        "cells": n ** 3,
+        "dof_per_cell_per_var": N,
+        "precision": precision,
+        "l2": f"state {5 * N * 8 * n ** 3 / 1e6:.0f} MB per buffer, larger than the 129 MB L2 (no flush needed)",
+    }
+
+
+# ------------------------------------------------------------ distributed
+def dist_init(use_cuda):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if use_cuda else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, v, device=None):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(world, v, device=None):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------- clocks
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons, power = [], None, set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+# ------------------------------------------------------------------ setup
+def build_state_host(args):
+    """Canonical initial state from the oracle's projection (reference arm)."""
+    import oracle
+    n = (args.n,) * 3
+    o = oracle.Oracle(n, args.order - 1, GAMMA)
+    fn = syn.solenoidal_velocity(seed=SEED, mach=MACH, gamma=GAMMA)
+    return o, o.project_fn(fn)
+
+
+def driving(args):
+    from paper_1602_09079_gb300.forcing import OUDriving
+    nv = syn.driving_modes(1.0, 2.0)
+    cs = math.sqrt(GAMMA * (1.0 / GAMMA) / 1.0)
+    t_s = 1.0 / (2.0 * MACH * cs)  # half the eddy turnover time, L = 1 (Sect. 3.1)
+    z = syn.ou_noise(SEED, 2, len(nv))
+    # amplitude: rms acceleration ~ (M c)^2 k_drive, the order that sustains
+    # rms Mach M against dissipation at the driving scale (fixed here; the
+    # paper rescales it to the target Mach number)
+    amp = (MACH * cs) ** 2 * 2 * math.pi * 1.5
+    drv = OUDriving(nv, t_s, 0.1 * t_s, amp, z[0])
+    drv.update(z[1])
+    return drv
+
+
+def roofline_entry(kind, achieved, peak, unit, bound, traffic=None):
+    return {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+            "frac": (achieved / peak) if peak else None, "traffic": traffic}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+# --------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    import paper_1602_09079_gb300 as dgm
+    from paper_1602_09079_gb300 import roofline as rl
+
+    world, rank, local = dist_init(True)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dgm.load()
+    n = (args.n,) * 3
+    k = args.order - 1
+    s = dgm.Solver(n, args.order, GAMMA, forcing=True)
+    N, nc = s.N, s.ncells
+    fn = syn.solenoidal_velocity(seed=SEED, mach=MACH, gamma=GAMMA)
+    s.project_fn(fn)
+    drv = driving(args)
+    s.set_forcing(drv.nvec, drv.ahat())
+    w0_dev = torch.from_numpy(s.get_state()).to(dev)
+    c_iso = math.sqrt(1.0 / GAMMA)  # p0/rho0 at the start state
+
+    def one_step():
+        dt = s.cfl_dt(args.courant)
+        s.step(dt)
+        s.energy_reset(c_iso, 1.0)
+
+    results = {}
+    precs = [p for p in ("fp64", "mixed") if p in args.precisions.split(",")]
+    for prec_name in precs:
+        prec = dgm.DG_PREC_FP64 if prec_name == "fp64" else dgm.DG_PREC_MIXED
+        s.set_precision(prec)
+        s.set_state(w0_dev)
+        for _ in range(args.warmup):
+            one_step()
+        s.check()
+        s.kernel_stats()  # reset counters
+        clocks = Clocks(local)
+        barrier(world)
+        torch.cuda.synchronize()
+        clocks.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s.stream)
+        for _ in range(args.steps):
+            one_step()
+        e1.record(s.stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        ck = clocks.stop()
+        s.check()
+        stats = s.kernel_stats()
+        ms = e0.elapsed_time(e1)
+        ms_max = max_over_ranks(world, ms, dev)
+        dof = float(nc) * N * 3 * args.steps
+        dof_all = sum_over_ranks(world, dof, dev)
+        # per-kernel timing pass (events around every launch, separate steps)
+        s.set_timing(True)
+        for _ in range(2):
+            one_step()
+        kst = s.kernel_stats()
+        s.set_timing(False)
+        results[prec_name] = {"ms": ms, "ms_max": ms_max, "dof_all": dof_all, "clocks": ck,
+                              "launches": stats, "ktimes": kst}
+
+    # mixed vs FP64 error at matched steps with a fixed dt
+    s.set_precision(dgm.DG_PREC_FP64)
+    s.set_state(w0_dev)
+    dt_fix = s.cfl_dt(args.courant)
+    err_steps = args.err_steps
+
+    def fixed_run(prec):
+        s.set_precision(prec)
+        s.set_state(w0_dev)
+        for _ in range(err_steps):
+            s.step(dt_fix)
+            s.energy_reset(c_iso, 1.0)
+        s.check()
+        return s.y.view(5, N, nc).clone()
+
+    l2 = mx = None
+    if err_steps > 0:
+        y64 = fixed_run(dgm.DG_PREC_FP64)
+        ymx = fixed_run(dgm.DG_PREC_MIXED)
+        d = ymx - y64
+        l2 = (torch.sqrt((d * d).sum(dim=(1, 2))) / torch.sqrt((y64 * y64).sum(dim=(1, 2)))).tolist()
+        mx = (d.abs().amax(dim=(1, 2)) / y64.abs().amax(dim=(1, 2))).tolist()
+        del y64, ymx, d
+
+    # end-to-end through the public API with host buffers
+    s.set_precision(dgm.DG_PREC_MIXED)
+    host_in = torch.from_numpy(w0_dev.cpu().numpy()).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        dgm.dg_set_state(s.ctx, host_in.data_ptr(), 0)
+        one_step()
+        dgm.dg_get_state(s.ctx, host_out.data_ptr(), 0)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_s = max(max_over_ranks(world, e2e_s, dev), 1e-30)
+    e2e_dof = sum_over_ranks(world, float(nc) * N * 3 * args.e2e_steps, dev)
+    state_bytes = 5 * N * nc * 8
+
+    # roofline of the dominant kernel (volume) from the live per-launch timing
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs")
+    fp64_probe = dgm.dg_probe_fma_peak(True)
+    fp32_probe = dgm.dg_probe_fma_peak(False)
+    # derived ALU peaks: 152 SMs x lanes x 2 flops x 2.07 GHz (FP32: 128 lanes);
+    # FP64 1.25 TFLOP/s (GB300 datasheet figure)
+    fp32_peak = 152 * 128 * 2 * 2.07e9
+    fp64_peak = 1.25e12
+
+    def kernel_roofline(prec_name, tsize):
+        kst = results[prec_name]["ktimes"]
+        nvol, msvol = kst["volume"]
+        per_launch_s = msvol / nvol * 1e-3
+        flops = rl.volume_flops(k, True) * nc
+        byts = rl.volume_bytes(k, tsize, True) * nc
+        t_alu = flops / (fp64_peak if tsize == 8 else fp32_peak)
+        t_hbm = byts / (hbm * 1e9) if hbm else 0.0
+        if t_alu >= t_hbm:
+            e = roofline_entry("alu", flops / per_launch_s / 1e12, (fp64_peak if tsize == 8 else fp32_peak) / 1e12,
+                               "TFLOP/s", "alu")
+            e["peak_source"] = ("derived: FP64 1.25 TFLOP/s datasheet" if tsize == 8 else
+                                "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz")
+        else:
+            e = roofline_entry("hbm", byts / per_launch_s / 1e9, hbm, "GB/s", "hbm")
+            e["peak_source"] = "measured (MEASURED_PEAKS.json hbm_gbs)"
+        e["kernel"] = f"volume_kernel<K={k}, {'double' if tsize == 8 else 'float'}, stage, forcing>"
+        e["flops_per_launch"] = flops
+        e["bytes_per_launch"] = byts
+        e["ms_per_launch"] = per_launch_s * 1e3
+        e["achieved_gbs"] = byts / per_launch_s / 1e9
+        e["achieved_tflops"] = flops / per_launch_s / 1e12
+        tot = sum(v[1] for v in kst.values())
+        e["share_of_step"] = {kk: (v[1] / tot if tot else None) for kk, v in kst.items()}
+        return e
+
+    head = "mixed" if "mixed" in results else "fp64"
+    r_mx = results[head]
+    r_64 = results.get("fp64", r_mx)
+    value = r_mx["dof_all"] / (r_mx["ms_max"] * 1e-3)
+    value64 = r_64["dof_all"] / (r_64["ms_max"] * 1e-3)
+    launches = sum(v[0] for v in r_mx["launches"].values())
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        cpu = cpu_baseline(args, s.get_state(), drv, budget=args.cpu_seconds)
+
+    if rank == 0:
+        out = {
+            "metric": "DG DOF-updates/sec per RK stage (FP32-mixed, FP64 RK accumulation; FP64 plain beside it)",
+            "value": value,
+            "unit": "DOF-updates/s",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": r_mx["ms_max"] / args.steps,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32 (f64 state and accumulation)" if head == "mixed" else "f64",
+            "data": "synthetic",
+            "config": workload_config(args, head),
+            "roofline": kernel_roofline(head, 4 if head == "mixed" else 8),
+            "fp64": {
+                "value": value64,
+                "unit": "DOF-updates/s",
+                "ms_per_step": r_64["ms_max"] / args.steps,
+                "dtype": "f64",
+                "roofline": kernel_roofline("fp64", 8) if "fp64" in results else None,
+                "clocks": r_64["clocks"],
+                "gpu_launches": sum(v[0] for v in r_64["launches"].values()),
+            },
+            "speedup_mixed_over_fp64": value / value64,
+            "mixed_vs_fp64_error": {"steps": err_steps, "dt": dt_fix,
+                                    "l2_rel_per_var": l2, "max_coef_rel_per_var": mx},
+            "e2e": {"value": e2e_dof / e2e_s, "unit": "DOF-updates/s",
+                    "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes,
+                    "note": "dg_set_state from pinned host + step + dg_get_state to pinned host, per step"},
+            "gpu_launches": launches,
+            "launches_by_class": {kk: v[0] for kk, v in r_mx["launches"].items()},
+            "clocks": r_mx["clocks"],
+            "probe_fma_tflops": {"fp64": fp64_probe / 1e12, "fp32": fp32_probe / 1e12},
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(out))
+    barrier(world)
+
+
+# ----------------------------------------------------------- CPU oracle
+def cpu_baseline(args, w_canon, drv, budget=12.0, sample=4096):
+    """The FP64 oracle on the host cores: R (all five variables) and the
+    limiter at a fixed random sample of cells of the same state, i.e. one RK
+    stage's work on the sample."""
+    import oracle
+    o = oracle.Oracle((args.n,) * 3, args.order - 1, GAMMA)
+    o.set_forcing(drv.nvec, drv.ahat())
+    cells = syn.sample_cells(o.ncells, sample, seed=3)
+    N = o.N
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        o.rhs_cells(w_canon, cells)
+        o.limit_cells(w_canon, cells)
+        reps += 1
+        if time.perf_counter() - t0 > budget:
+            break
+    dt = (time.perf_counter() - t0) / reps
+    return {"value": len(cells) * N / dt, "unit": "DOF-updates/s", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"R + limiter on {len(cells)} random cells of the {args.n}^3 state, {reps} reps"}
+
+
+def run_reference(args):
+    world, rank, local = dist_init(False)
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    o, w = build_state_host(args)
+    drv = driving(args)
+    o.set_forcing(drv.nvec, drv.ahat())
+    cells = syn.sample_cells(o.ncells, 8192, seed=3)
+    for _ in range(args.warmup):
+        o.rhs_cells(w, cells)
+        o.limit_cells(w, cells)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.rhs_cells(w, cells)
+        o.limit_cells(w, cells)
+    el = time.perf_counter() - t0
+    value = len(cells) * o.N * args.steps / el
+    sample = f"R + limiter on {len(cells)} random cells of the {args.n}^3 state per step"
+    print(json.dumps({
+        "impl": "reference",
+        "metric": "DG DOF-updates/sec per RK stage (FP32-mixed, FP64 RK accumulation; FP64 plain beside it)",
+        "value": value, "unit": "DOF-updates/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args, "fp64 (CPU oracle)"),
+        "cpu_baseline": {"value": value, "unit": "DOF-updates/s", "cores": oracle.num_threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "DOF-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -165,6 +165,26 @@ int dg_totals(dg_ctx* ctx, double* out5);
  * word. */
 int dg_check(dg_ctx* ctx);
 
+/* ---- measurement aids (no counterpart in the paper) --------------------
+ * Kernel classes: 0 limiter, 1 face flux, 2 volume (RHS or fused stage),
+ * 3 CFL reduction, 4 energy reset, 5 other (layout, projection, sums). */
+#define DG_KCLASS_COUNT 6
+
+/* When on != 0, every kernel the context launches is bracketed by CUDA
+ * events recorded on the bound stream (adds two event records per launch). */
+int dg_set_timing(dg_ctx* ctx, int on);
+
+/* Per class: launches since the last call (always counted) and, if timing
+ * was on, their summed device time in ms (0 otherwise). Synchronises the
+ * stream; resets the counters. Arrays of DG_KCLASS_COUNT entries, either may
+ * be NULL. */
+int dg_kernel_stats(dg_ctx* ctx, int64_t* launches, double* ms);
+
+/* Dense FMA throughput of the current device in FLOP/s (fp64 != 0: FP64,
+ * else FP32), measured by a register-resident FMA loop over all SMs timed
+ * with CUDA events; takes tens of milliseconds. */
+int dg_probe_fma_peak(int fp64, double* flops_per_s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -57,7 +57,13 @@ _SIGS = {
     "dg_energy_reset": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.POINTER(C.c_double)]),
     "dg_totals": (C.c_int, [C.c_void_p, C.c_void_p]),
     "dg_check": (C.c_int, [C.c_void_p]),
+    "dg_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
+    "dg_kernel_stats": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "dg_probe_fma_peak": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
 }
+
+DG_KCLASS_COUNT = 6
+KERNEL_CLASSES = ("limiter", "face_flux", "volume", "cfl", "energy_reset", "other")
 
 
 def library_path() -> str:
@@ -197,6 +203,24 @@ def dg_check(ctx):
     _check(load().dg_check(ctx), "dg_check")
 
 
+def dg_set_timing(ctx, on):
+    _check(load().dg_set_timing(ctx, int(bool(on))), "dg_set_timing")
+
+
+def dg_kernel_stats(ctx):
+    """{class: (launches, ms)} since the last call; synchronises."""
+    n = np.zeros(DG_KCLASS_COUNT, dtype=np.int64)
+    ms = np.zeros(DG_KCLASS_COUNT)
+    _check(load().dg_kernel_stats(ctx, n.ctypes.data, ms.ctypes.data), "dg_kernel_stats")
+    return {name: (int(n[i]), float(ms[i])) for i, name in enumerate(KERNEL_CLASSES)}
+
+
+def dg_probe_fma_peak(fp64):
+    v = C.c_double(0.0)
+    _check(load().dg_probe_fma_peak(int(bool(fp64)), C.byref(v)), "dg_probe_fma_peak")
+    return v.value
+
+
 # ------------------------------------------------------------- convenience
 
 def nmodes(k: int) -> int:
@@ -310,3 +334,9 @@ class Solver:
 
     def check(self):
         dg_check(self.ctx)
+
+    def set_timing(self, on):
+        dg_set_timing(self.ctx, on)
+
+    def kernel_stats(self):
+        return dg_kernel_stats(self.ctx)

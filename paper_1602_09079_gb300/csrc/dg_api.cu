@@ -297,6 +297,15 @@ struct dg_ctx {
   double* ybuf = nullptr;
   void* fh = nullptr;
   void* field = nullptr;
+  // measurement: launch counts per kernel class, optional event timing
+  bool timing = false;
+  long long launches[DG_KCLASS_COUNT] = {};
+  struct Pending {
+    int cls;
+    cudaEvent_t a, b;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> pool;
   // settings
   int prec = DG_PREC_FP64;
   bool limited = false;
@@ -370,10 +379,63 @@ int sync_and_check(dg_ctx* c, Ctrl* host_copy) {
 
 int set_device(const dg_ctx* c) { return cuda_ok(cudaSetDevice(c->device)); }
 
+cudaEvent_t take_event(dg_ctx* c) {
+  if (!c->pool.empty()) {
+    cudaEvent_t e = c->pool.back();
+    c->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Every kernel launch of a context goes through here: counted per class and,
+// with timing on, bracketed by events on the bound stream.
+template <class F>
+int launch(dg_ctx* c, int cls, F&& f) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (c->timing) {
+    a = take_event(c);
+    b = take_event(c);
+    if (!a || !b) return DG_ERR_CUDA;
+    DG_CUDA(cudaEventRecord(a, c->stream));
+  }
+  cudaError_t e = f();
+  c->launches[cls] += 1;
+  if (c->timing) {
+    DG_CUDA(cudaEventRecord(b, c->stream));
+    c->pending.push_back({cls, a, b});
+  }
+  return cuda_ok(e);
+}
+
+enum { KC_LIMIT = 0, KC_FACE = 1, KC_VOLUME = 2, KC_CFL = 3, KC_RESET = 4, KC_OTHER = 5 };
+
 int refresh_field(dg_ctx* c) {
   if (c->n_force == 0) return DG_OK;
-  DG_CUDA(c->fn.forcing_field(c->prec, c->field, c->modes_dev, c->n_force, c->geo, c->L, c->stream));
-  return DG_OK;
+  return launch(c, KC_OTHER, [&] {
+    return c->fn.forcing_field(c->prec, c->field, c->modes_dev, c->n_force, c->geo, c->L, c->stream);
+  });
+}
+
+// dense FMA throughput probe: 8 independent chains per thread
+__device__ double g_probe_sink64;
+__device__ float g_probe_sink32;
+
+template <typename T>
+__global__ void __launch_bounds__(256) fma_probe_kernel(int iters, T a, T b, int write) {
+  T x0 = (T)threadIdx.x * (T)1e-3, x1 = x0 + (T)1, x2 = x0 + (T)2, x3 = x0 + (T)3;
+  T x4 = x0 + (T)4, x5 = x0 + (T)5, x6 = x0 + (T)6, x7 = x0 + (T)7;
+  for (int i = 0; i < iters; ++i) {
+    x0 = fma(x0, a, b); x1 = fma(x1, a, b); x2 = fma(x2, a, b); x3 = fma(x3, a, b);
+    x4 = fma(x4, a, b); x5 = fma(x5, a, b); x6 = fma(x6, a, b); x7 = fma(x7, a, b);
+  }
+  T s = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
+  if (write) {
+    if (sizeof(T) == 8) g_probe_sink64 = (double)s;
+    else g_probe_sink32 = (float)s;
+  }
 }
 
 }  // namespace
@@ -432,7 +494,15 @@ int dg_init(const dg_mesh* mesh, int order, double gamma, dg_ctx** out) {
   return DG_OK;
 }
 
-void dg_destroy(dg_ctx* c) { delete c; }
+void dg_destroy(dg_ctx* c) {
+  if (!c) return;
+  for (auto& p : c->pending) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  for (auto e : c->pool) cudaEventDestroy(e);
+  delete c;
+}
 
 int dg_sizes(const dg_ctx* c, int features, size_t* state_len, size_t* scratch_bytes) {
   if (!c) return DG_ERR_ARG;
@@ -478,8 +548,10 @@ int dg_set_state(dg_ctx* c, const double* src, int is_device) {
     canon = c->ybuf;
   }
   dim3 grid((unsigned)((c->geo.nc + 31) / 32), (R + 31) / 32);
-  canon_to_state_kernel<<<grid, dim3(32, 8), 0, c->stream>>>(canon, c->y, c->geo.nc, R);
-  DG_CUDA(cudaGetLastError());
+  DG_TRY(launch(c, KC_OTHER, [&] {
+    canon_to_state_kernel<<<grid, dim3(32, 8), 0, c->stream>>>(canon, c->y, c->geo.nc, R);
+    return cudaGetLastError();
+  }));
   c->limited = false;
   return DG_OK;
 }
@@ -491,8 +563,10 @@ int dg_get_state(dg_ctx* c, double* dst, int is_device) {
   const int R = 5 * c->N;
   double* canon = is_device ? dst : c->ybuf;
   dim3 grid((unsigned)((c->geo.nc + 31) / 32), (R + 31) / 32);
-  state_to_canon_kernel<<<grid, dim3(32, 8), 0, c->stream>>>(c->y, canon, c->geo.nc, R);
-  DG_CUDA(cudaGetLastError());
+  DG_TRY(launch(c, KC_OTHER, [&] {
+    state_to_canon_kernel<<<grid, dim3(32, 8), 0, c->stream>>>(c->y, canon, c->geo.nc, R);
+    return cudaGetLastError();
+  }));
   if (!is_device) {
     DG_CUDA(cudaMemcpyAsync(dst, c->ybuf, sizeof(double) * R * c->geo.nc, cudaMemcpyDeviceToHost, c->stream));
     DG_CUDA(cudaStreamSynchronize(c->stream));
@@ -526,7 +600,7 @@ int dg_project(dg_ctx* c, const double* q_points_dev) {
   DG_TRY(need_bound(c));
   if (!q_points_dev) return DG_ERR_ARG;
   DG_TRY(set_device(c));
-  DG_CUDA(c->fn.project(q_points_dev, c->y, c->geo, c->stream));
+  DG_TRY(launch(c, KC_OTHER, [&] { return c->fn.project(q_points_dev, c->y, c->geo, c->stream); }));
   c->limited = false;
   return DG_OK;
 }
@@ -537,8 +611,10 @@ int dg_rhs(dg_ctx* c, const double* y_dev, double* R_dev) {
   DG_TRY(set_device(c));
   const double* y = y_dev ? y_dev : c->y;
   const bool force = c->n_force > 0;
-  DG_CUDA(c->fn.face(c->prec, y, c->fh, c->geo, c->stream));
-  DG_CUDA(c->fn.volume_rhs(c->prec, force, y, c->fh, c->field, c->geo, R_dev, c->ctrl, c->stream));
+  DG_TRY(launch(c, KC_FACE, [&] { return c->fn.face(c->prec, y, c->fh, c->geo, c->stream); }));
+  DG_TRY(launch(c, KC_VOLUME, [&] {
+    return c->fn.volume_rhs(c->prec, force, y, c->fh, c->field, c->geo, R_dev, c->ctrl, c->stream);
+  }));
   return DG_OK;
 }
 
@@ -547,7 +623,8 @@ int dg_step(dg_ctx* c, double dt) {
   if (!(dt > 0.0) || !std::isfinite(dt)) return DG_ERR_ARG;
   DG_TRY(set_device(c));
   const bool force = c->n_force > 0;
-  if (!c->limited) DG_CUDA(c->fn.limit(c->y, nullptr, c->geo, c->ctrl, c->stream));
+  if (!c->limited)
+    DG_TRY(launch(c, KC_LIMIT, [&] { return c->fn.limit(c->y, nullptr, c->geo, c->ctrl, c->stream); }));
   // Shu-Osher SSP-RK3: y1 = y0 - dt R(y0); y2 = 3/4 y0 + 1/4 (y1 - dt R(y1));
   // y3 = 1/3 y0 + 2/3 (y2 - dt R(y2)); each output limited for the next stage.
   const double a0[3] = {0.0, 0.75, 1.0 / 3.0};
@@ -555,9 +632,11 @@ int dg_step(dg_ctx* c, double dt) {
   const double* ys = c->y;
   for (int s = 0; s < 3; ++s) {
     double* out = s < 2 ? c->ybuf : c->y;
-    DG_CUDA(c->fn.face(c->prec, ys, c->fh, c->geo, c->stream));
-    DG_CUDA(c->fn.volume_stage(c->prec, force, c->fh, c->field, c->geo, ys, c->y, out, a0[s], b0[s], dt, c->ctrl,
-                               c->stream));
+    DG_TRY(launch(c, KC_FACE, [&] { return c->fn.face(c->prec, ys, c->fh, c->geo, c->stream); }));
+    DG_TRY(launch(c, KC_VOLUME, [&] {
+      return c->fn.volume_stage(c->prec, force, c->fh, c->field, c->geo, ys, c->y, out, a0[s], b0[s], dt, c->ctrl,
+                                c->stream);
+    }));
     ys = out;
   }
   c->limited = true;
@@ -568,7 +647,7 @@ int dg_limit(dg_ctx* c, int8_t* flags_dev, int64_t* n_limited) {
   DG_TRY(need_bound(c));
   DG_TRY(set_device(c));
   if (n_limited) DG_CUDA(cudaMemsetAsync(&c->ctrl->n_limited, 0, sizeof(unsigned long long), c->stream));
-  DG_CUDA(c->fn.limit(c->y, flags_dev, c->geo, c->ctrl, c->stream));
+  DG_TRY(launch(c, KC_LIMIT, [&] { return c->fn.limit(c->y, flags_dev, c->geo, c->ctrl, c->stream); }));
   c->limited = true;
   if (n_limited) {
     Ctrl h{};
@@ -584,7 +663,7 @@ int dg_cfl_dt(dg_ctx* c, double courant, double* dt_out) {
   if (!dt_out || !(courant > 0.0)) return DG_ERR_ARG;
   DG_TRY(set_device(c));
   DG_CUDA(cudaMemsetAsync(&c->ctrl->cfl_max_bits, 0, sizeof(unsigned long long), c->stream));
-  DG_CUDA(c->fn.cfl(c->y, c->geo, c->ctrl, c->stream));
+  DG_TRY(launch(c, KC_CFL, [&] { return c->fn.cfl(c->y, c->geo, c->ctrl, c->stream); }));
   Ctrl h{};
   int st = sync_and_check(c, &h);
   if (st != DG_OK) return st;
@@ -648,12 +727,16 @@ int dg_energy_reset(dg_ctx* c, double c_iso, double rho0, double* dissipated) {
   DG_TRY(set_device(c));
   int n_part = 0;
   const double c2g = c_iso * c_iso / (c->geo.gamma - 1.0);
-  DG_CUDA(c->fn.energy_reset(c->prec, c->y, c->geo, c2g, 1.0 / rho0, c->part, &n_part, c->ctrl, c->stream));
+  DG_TRY(launch(c, KC_RESET, [&] {
+    return c->fn.energy_reset(c->prec, c->y, c->geo, c2g, 1.0 / rho0, c->part, &n_part, c->ctrl, c->stream);
+  }));
   c->limited = true;
   if (dissipated) {
     const double vol = c->geo.dx[0] * c->geo.dx[1] * c->geo.dx[2];
-    sum_rows_kernel<<<1, 256, 0, c->stream>>>(c->part, n_part, vol, c->sums);
-    DG_CUDA(cudaGetLastError());
+    DG_TRY(launch(c, KC_OTHER, [&] {
+      sum_rows_kernel<<<1, 256, 0, c->stream>>>(c->part, n_part, vol, c->sums);
+      return cudaGetLastError();
+    }));
     double h = 0.0;
     DG_CUDA(cudaMemcpyAsync(&h, c->sums, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     int st = sync_and_check(c, nullptr);
@@ -669,11 +752,15 @@ int dg_totals(dg_ctx* c, double* out5) {
   DG_TRY(set_device(c));
   long long nb = (c->geo.nc + 255) / 256;
   const int G = (int)(nb < kRedBlocks ? nb : kRedBlocks);
-  means_partial_kernel<<<G, 256, 0, c->stream>>>(c->y, c->geo.nc, c->N, c->part);
-  DG_CUDA(cudaGetLastError());
+  DG_TRY(launch(c, KC_OTHER, [&] {
+    means_partial_kernel<<<G, 256, 0, c->stream>>>(c->y, c->geo.nc, c->N, c->part);
+    return cudaGetLastError();
+  }));
   const double vol = c->geo.dx[0] * c->geo.dx[1] * c->geo.dx[2];
-  sum_rows_kernel<<<5, 256, 0, c->stream>>>(c->part, G, vol, c->sums);
-  DG_CUDA(cudaGetLastError());
+  DG_TRY(launch(c, KC_OTHER, [&] {
+    sum_rows_kernel<<<5, 256, 0, c->stream>>>(c->part, G, vol, c->sums);
+    return cudaGetLastError();
+  }));
   DG_CUDA(cudaMemcpyAsync(out5, c->sums, sizeof(double) * 5, cudaMemcpyDeviceToHost, c->stream));
   return sync_and_check(c, nullptr);
 }
@@ -682,6 +769,69 @@ int dg_check(dg_ctx* c) {
   DG_TRY(need_bound(c));
   DG_TRY(set_device(c));
   return sync_and_check(c, nullptr);
+}
+
+int dg_set_timing(dg_ctx* c, int on) {
+  if (!c) return DG_ERR_ARG;
+  c->timing = on != 0;
+  return DG_OK;
+}
+
+int dg_kernel_stats(dg_ctx* c, int64_t* launches, double* ms) {
+  if (!c) return DG_ERR_ARG;
+  double acc[DG_KCLASS_COUNT] = {};
+  int st = DG_OK;
+  if (c->bound) {
+    DG_TRY(set_device(c));
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) st = DG_ERR_CUDA;
+  }
+  for (auto& p : c->pending) {
+    float t = 0.f;
+    if (st == DG_OK && cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) acc[p.cls] += t;
+    c->pool.push_back(p.a);
+    c->pool.push_back(p.b);
+  }
+  c->pending.clear();
+  for (int i = 0; i < DG_KCLASS_COUNT; ++i) {
+    if (launches) launches[i] = c->launches[i];
+    if (ms) ms[i] = acc[i];
+    c->launches[i] = 0;
+  }
+  return st;
+}
+
+int dg_probe_fma_peak(int fp64, double* flops_per_s) {
+  if (!flops_per_s) return DG_ERR_ARG;
+  int dev = 0, sms = 0;
+  DG_CUDA(cudaGetDevice(&dev));
+  DG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int blocks = sms * 8, threads = 256;
+  const int iters = fp64 ? 4096 : 4096 * 64;
+  cudaEvent_t a, b;
+  DG_CUDA(cudaEventCreate(&a));
+  DG_CUDA(cudaEventCreate(&b));
+  float best = 1e30f;
+  for (int rep = 0; rep < 3; ++rep) {
+    cudaEventRecord(a, 0);
+    if (fp64)
+      fma_probe_kernel<double><<<blocks, threads>>>(iters, 0.999999, 1e-7, 0);
+    else
+      fma_probe_kernel<float><<<blocks, threads>>>(iters, 0.999999f, 1e-7f, 0);
+    cudaEventRecord(b, 0);
+    if (cudaEventSynchronize(b) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+      return DG_ERR_CUDA;
+    }
+    float t = 0.f;
+    cudaEventElapsedTime(&t, a, b);
+    if (rep > 0 && t < best) best = t;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  const double flops = 2.0 * 8.0 * (double)iters * blocks * threads;
+  *flops_per_s = flops / (best * 1e-3);
+  return DG_OK;
 }
 
 }  // extern "C"

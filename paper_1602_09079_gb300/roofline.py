@@ -1,0 +1,73 @@
+"""Algorithmic work of the DG kernels, counted from their loop bounds.
+
+Per cell and per RK stage (k = degree, N = N(k), Q = k+1, Q2 = Q^2,
+Q3 = Q^3; FMA = 2 flops; sqrt and division count as one flop each):
+
+face_flux_kernel (3 faces per cell, Q2 points each)
+    traces of both sides  2 x 5 x N FMA           -> 20 N
+    HLLC flux                                      -> HLLC_FLOPS
+volume_kernel
+    point values          Q3 x 5 N FMA            -> 10 N Q3
+    Euler fluxes, scaling Q3 x 46                  (1 div, velocity,
+                                                    pressure, 3 fluxes, 1/dx)
+    source                Q3 x 8                   (forcing only)
+    volume projection     5 x 3 Q3 N FMA           -> 30 Q3 N
+    source projection     4 x Q3 N FMA             -> 8 Q3 N (forcing only)
+    face projection       5 x 3 Q2 (2 + 2 N FMA)   -> 15 Q2 (2 + 4 N)
+    stage combination     5 N x 5                  (RK stage only)
+    limiter screen        ~ 10 N + 30              (RK stage only)
+
+Algorithmic HBM bytes (unique data each launch must touch):
+    face:   read y_s (5 N x 8) + write face fluxes (15 Q2 x sizeof(T))
+    volume: read y_s, y_0 (stages 2-3), face fluxes, forcing field
+            (3 Q3 x sizeof(T)), write y_{s+1} (5 N x 8 each)
+"""
+from __future__ import annotations
+
+HLLC_FLOPS = 116
+
+
+def _dims(k):
+    N = (k + 1) * (k + 2) * (k + 3) // 6
+    Q = k + 1
+    return N, Q, Q * Q, Q * Q * Q
+
+
+def face_flops(k):
+    N, Q, Q2, Q3 = _dims(k)
+    return 3 * Q2 * (20 * N + HLLC_FLOPS)
+
+
+def volume_flops(k, forcing, stage=True):
+    N, Q, Q2, Q3 = _dims(k)
+    f = 10 * N * Q3 + 46 * Q3 + 30 * Q3 * N + 15 * Q2 * (2 + 4 * N)
+    if forcing:
+        f += 8 * Q3 + 8 * Q3 * N
+    if stage:
+        f += 25 * N + 10 * N + 30
+    return f
+
+
+def face_bytes(k, tsize):
+    N, Q, Q2, Q3 = _dims(k)
+    return 5 * N * 8 + 15 * Q2 * tsize
+
+
+def volume_bytes(k, tsize, forcing, reads_y0=True):
+    N, Q, Q2, Q3 = _dims(k)
+    b = 5 * N * 8 * (3 if reads_y0 else 2) + 15 * Q2 * tsize
+    if forcing:
+        b += 3 * Q3 * tsize
+    return b
+
+
+def step_flops(k, forcing):
+    """Per cell per SSP-RK3 step (3 stages), both RHS kernels."""
+    return 3 * (face_flops(k) + volume_flops(k, forcing))
+
+
+def step_min_bytes(k):
+    """Minimum HBM traffic per cell per step of a fully fused stage: read
+    y_s, read y_0 on stages 2-3, write y_{s+1} (FP64 state)."""
+    N = (k + 1) * (k + 2) * (k + 3) // 6
+    return (3 + 2 + 3) * 5 * N * 8
