@@ -52,6 +52,7 @@ extern "C" {
 #define DG_ERR_NONFINITE -4    /* NaN/Inf found in the state */
 #define DG_ERR_POSITIVITY -5   /* a cell mean density or pressure below eps */
 #define DG_ERR_NEWTON -6       /* limiter Newton iteration did not converge */
+#define DG_ERR_TOO_LARGE -7    /* problem exceeds dg_rhs_noalloc's fixed scratch */
 
 #define DG_PREC_FP64 0   /* every step in FP64 */
 #define DG_PREC_MIXED 1  /* quadrature, fluxes and projection in FP32; RK
@@ -179,6 +180,32 @@ int dg_set_timing(dg_ctx* ctx, int on);
  * stream; resets the counters. Arrays of DG_KCLASS_COUNT entries, either may
  * be NULL. */
 int dg_kernel_stats(dg_ctx* ctx, int64_t* launches, double* ms);
+
+/* ---- allocation-free entry point (no counterpart in the paper) ---------
+ * R(y) exactly as dg_rhs computes it (same kernels; no driving source), for
+ * callers that must not allocate device memory themselves: code whose device
+ * memory is owned and budgeted by a host application or another framework's
+ * allocator, where a cudaMalloc (or the implicit synchronisation of a
+ * cudaFree) is not allowed during the run. Instead of a caller-allocated
+ * scratch, the face fluxes go to one fixed array in device memory,
+ * DG_NOALLOC_SCRATCH_BYTES = 32 MiB, that every GPU which loads the library
+ * holds until the process exits. Needs 15 (k+1)^2 n_cells x 8 bytes (FP64)
+ * or x 4 bytes (DG_PREC_MIXED), plus 256: e.g. at most 31,000 cells at
+ * order 3 in FP64; larger problems return DG_ERR_TOO_LARGE.
+ * mesh/order/gamma as in dg_init; precision DG_PREC_FP64 or DG_PREC_MIXED;
+ * y_dev (input) and R_dev (output): device, state layout, 5 N n_cells doubles;
+ * cuda_stream: cudaStream_t (NULL = legacy default stream), enqueued without
+ * synchronising. No context, no dg_bind, no cudaMalloc/cudaFree or any
+ * allocating library call. The first call on a device looks up the array's
+ * device address and uploads the basis tables of that order (a synchronous
+ * copy), so make the first call for each device and order before any stream
+ * capture. All calls share the one array: calls that overlap on the GPU (on
+ * different streams, or from several threads) race on it; serialise them.
+ * The array keeps the last call's contents; every entry a call reads is
+ * written by the same call first. */
+#define DG_NOALLOC_SCRATCH_BYTES (32u << 20)
+int dg_rhs_noalloc(const dg_mesh* mesh, int order, double gamma, int precision, const double* y_dev,
+                   double* R_dev, void* cuda_stream);
 
 /* Dense FMA throughput of the current device in FLOP/s (fp64 != 0: FP64,
  * else FP32), measured by a register-resident FMA loop over all SMs timed

@@ -19,7 +19,7 @@ import numpy as np
 from . import _build
 
 DG_OK, DG_ERR_ARG, DG_ERR_NOT_BOUND, DG_ERR_CUDA = 0, -1, -2, -3
-DG_ERR_NONFINITE, DG_ERR_POSITIVITY, DG_ERR_NEWTON = -4, -5, -6
+DG_ERR_NONFINITE, DG_ERR_POSITIVITY, DG_ERR_NEWTON, DG_ERR_TOO_LARGE = -4, -5, -6, -7
 DG_PREC_FP64, DG_PREC_MIXED = 0, 1
 DG_FEATURE_FORCING = 1
 
@@ -60,6 +60,8 @@ _SIGS = {
     "dg_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
     "dg_kernel_stats": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "dg_probe_fma_peak": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
+    "dg_rhs_noalloc": (C.c_int, [C.POINTER(dg_mesh), C.c_int, C.c_double, C.c_int, C.c_void_p, C.c_void_p,
+                                 C.c_void_p]),
 }
 
 DG_KCLASS_COUNT = 6
@@ -213,6 +215,17 @@ def dg_kernel_stats(ctx):
     ms = np.zeros(DG_KCLASS_COUNT)
     _check(load().dg_kernel_stats(ctx, n.ctypes.data, ms.ctypes.data), "dg_kernel_stats")
     return {name: (int(n[i]), float(ms[i])) for i, name in enumerate(KERNEL_CLASSES)}
+
+
+def dg_rhs_noalloc(n, order, gamma, precision, y_dev, R_dev, stream, length=(1.0, 1.0, 1.0)):
+    """R(y) into R_dev using the library's fixed device scratch instead of a
+    caller allocation (see include/dg.h)."""
+    m = dg_mesh()
+    for a in range(3):
+        m.n[a] = int(n[a])
+        m.length[a] = float(length[a])
+    _check(load().dg_rhs_noalloc(C.byref(m), int(order), float(gamma), int(precision), _ptr(y_dev), _ptr(R_dev),
+                                 _ptr(stream)), "dg_rhs_noalloc")
 
 
 def dg_probe_fma_peak(fp64):

@@ -451,6 +451,7 @@ const char* dg_strerror(int code) {
     case DG_ERR_NONFINITE: return "non-finite value in the state";
     case DG_ERR_POSITIVITY: return "cell mean density or pressure below the positivity floor";
     case DG_ERR_NEWTON: return "positivity-limiter Newton iteration did not converge";
+    case DG_ERR_TOO_LARGE: return "problem too large for dg_rhs_noalloc's fixed 32 MiB device scratch";
     default: return "unknown status";
   }
 }
@@ -835,3 +836,83 @@ int dg_probe_fma_peak(int fp64, double* flops_per_s) {
 }
 
 }  // extern "C"
+
+// --------------------------------------------------------------------------
+// Allocation-free R(y): the face fluxes of dg_rhs go to one file-scope device
+// array instead of a caller-allocated scratch (for callers that may not
+// allocate device memory). The array name is a host-side stand-in in host
+// code; its device address comes from cudaGetSymbolAddress, looked up once
+// per device with that device current.
+namespace {
+
+constexpr size_t kNoAllocBytes = DG_NOALLOC_SCRATCH_BYTES;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+std::mutex g_noalloc_mu;
+void* g_noalloc_dev_ptr[64] = {};
+// host staging for a first-call table upload (static: no heap allocation)
+double g_noalloc_tab64[TAB_STRIDE];
+float g_noalloc_tab32[TAB_STRIDE];
+
+int noalloc_setup(int dev, int k, void** scratch) {
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_dev_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return DG_ERR_CUDA;
+    g_noalloc_dev_ptr[dev] = p;
+  }
+  *scratch = g_noalloc_dev_ptr[dev];
+  std::lock_guard<std::mutex> lock2(g_upload_mu);
+  if (!((g_uploaded[k] >> dev) & 1ull)) {
+    switch (k) {
+      case 0: build_tables<0>(g_noalloc_tab64); break;
+      case 1: build_tables<1>(g_noalloc_tab64); break;
+      case 2: build_tables<2>(g_noalloc_tab64); break;
+      default: build_tables<3>(g_noalloc_tab64); break;
+    }
+    for (int i = 0; i < TAB_STRIDE; ++i) g_noalloc_tab32[i] = (float)g_noalloc_tab64[i];
+    if (launchers_for(k).upload(g_noalloc_tab64, g_noalloc_tab32) != cudaSuccess) return DG_ERR_CUDA;
+    g_uploaded[k] |= 1ull << dev;
+  }
+  return DG_OK;
+}
+
+}  // namespace
+
+extern "C" int dg_rhs_noalloc(const dg_mesh* mesh, int order, double gamma, int precision, const double* y_dev,
+                              double* R_dev, void* cuda_stream) {
+  if (!mesh || !y_dev || !R_dev || order < 1 || order > 4 || !(gamma > 1.0) || !std::isfinite(gamma) ||
+      (precision != DG_PREC_FP64 && precision != DG_PREC_MIXED))
+    return DG_ERR_ARG;
+  Geo g{};
+  long long nc = 1;
+  for (int a = 0; a < 3; ++a) {
+    if (mesh->n[a] < 1 || !(mesh->length[a] > 0.0) || !std::isfinite(mesh->length[a])) return DG_ERR_ARG;
+    nc *= mesh->n[a];
+    g.dx[a] = mesh->length[a] / mesh->n[a];
+    g.inv_dx[a] = 1.0 / g.dx[a];
+  }
+  const int k = order - 1, Q = k + 1;
+  const size_t tsize = precision == DG_PREC_MIXED ? sizeof(float) : sizeof(double);
+  const size_t ctrl_bytes = 256;
+  if (nc > (long long)(kNoAllocBytes / tsize) ||
+      ctrl_bytes + (size_t)15 * Q * Q * (size_t)nc * tsize > kNoAllocBytes)
+    return DG_ERR_TOO_LARGE;
+  g.nx = mesh->n[0];
+  g.ny = mesh->n[1];
+  g.nz = mesh->n[2];
+  g.nc = nc;
+  g.gamma = gamma;
+  g.eps_rho = 1e-12;
+  g.eps_p = 1e-12;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return DG_ERR_CUDA;
+  void* scratch = nullptr;
+  DG_TRY(noalloc_setup(dev, k, &scratch));
+  Ctrl* ctrl = static_cast<Ctrl*>(scratch);
+  void* fh = static_cast<unsigned char*>(scratch) + ctrl_bytes;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  const Launchers L = launchers_for(k);
+  DG_CUDA(L.face(precision, y_dev, fh, g, s));
+  DG_CUDA(L.volume_rhs(precision, false, y_dev, fh, nullptr, g, R_dev, ctrl, s));
+  return DG_OK;
+}
