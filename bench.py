@@ -344,6 +344,7 @@ def run_ours(args):
         e["achieved_tflops"] = flops / per_launch_s / 1e12
         tot = sum(v[1] for v in kst.values())
         e["share_of_step"] = {kk: (v[1] / tot if tot else None) for kk, v in kst.items()}
+        e["ms_per_launch_by_class"] = {kk: (v[1] / v[0] if v[0] else None) for kk, v in kst.items()}
         return e
 
     head = "mixed" if "mixed" in results else "fp64"

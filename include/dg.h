@@ -181,6 +181,63 @@ int dg_set_timing(dg_ctx* ctx, int on);
  * be NULL. */
 int dg_kernel_stats(dg_ctx* ctx, int64_t* launches, double* ms);
 
+/* ---- learned troubled-cell indicator -----------------------------------
+ * No counterpart in the paper: a small network that predicts, per cell, the
+ * flag of the positivity limiter's indicator (Sect. 2.5: the polynomial
+ * leaves the positive set on S). Inputs per cell: the high modes scaled by the
+ * cell means, log(rho), the mean Mach number, and the 26 neighbour means
+ * relative to the cell's (include/dg.h order: own modes variable-major,
+ * then the two scalars, then neighbours (dz,dy,dx) lexicographic in
+ * {-1,0,1}^3 without the centre, variable-minor), zero-padded to a multiple
+ * of 32, in BF16. Network F -> 64 -> 64 -> 1 (ReLU, sigmoid); parameters FP32,
+ * flat: W1[64][F], b1[64], W2[64][64], b2[64], w3[64], b3. Orders 2..4. */
+
+/* Feature count, padded width F, parameter count, and the work-buffer bytes
+ * dg_indicator_backward needs. */
+int dg_indicator_sizes(int order, int* n_features, int* n_padded, size_t* n_params, size_t* work_bytes);
+
+/* Features of every cell of a state (state layout; NULL = the bound state)
+ * into X_dev, BF16 [n_cells][F], on the bound stream. */
+int dg_indicator_features(dg_ctx* ctx, const double* y_dev, uint16_t* X_dev);
+
+/* logits_dev[r] = network(X_dev[r]) for r < n (FP32), on cuda_stream. */
+int dg_indicator_forward(int order, const uint16_t* X_dev, int64_t n, const float* params_dev, float* logits_dev,
+                         void* cuda_stream);
+
+/* Gradient of the class-weighted binary cross entropy
+ * (1/n) sum_r [pos_weight y_r softplus(-z_r) + (1 - y_r) softplus(z_r)]
+ * with respect to every parameter into grads_dev (n_params floats), the loss
+ * in grads_dev[n_params]. labels_dev: n floats in {0, 1}. work_dev: at least
+ * work_bytes (dg_indicator_sizes). Deterministic (fixed reduction order). */
+int dg_indicator_backward(int order, const uint16_t* X_dev, const float* labels_dev, int64_t n, float pos_weight,
+                          const float* params_dev, float* grads_dev, void* work_dev, size_t work_bytes,
+                          void* cuda_stream);
+
+/* Gate the full positivity limiter with the indicator (params_dev: FP32
+ * parameters, caller-owned, valid while set; NULL switches the gate off).
+ * In every stage of dg_step, cells that fail the limiter's screen (the
+ * plain indicator's cheap sufficient test) are evaluated by the network;
+ * only those with probability >= threshold (0 < threshold < 1) go through
+ * the full limiter. The limiter itself is unchanged; cells the network
+ * passes over are not limited (its misses). */
+int dg_set_indicator(dg_ctx* ctx, const float* params_dev, float threshold);
+
+/* Training data from the bound state: one unlimited forward-Euler stage
+ * y1 = y - dt R(y) (current precision), its features (X_dev, BF16
+ * [n_cells][F]), whether each cell fails the limiter screen (screen_dev,
+ * uint8 0/1) and the limiter's flags on y1 (flags_dev, int8: bit0 theta1 < 1,
+ * bit1 theta2 < 1). The bound state is unchanged. Synchronises. */
+int dg_indicator_capture(dg_ctx* ctx, double dt, uint16_t* X_dev, int8_t* flags_dev, uint8_t* screen_dev);
+
+/* Limiter work since the last call (synchronises, then resets): cells that
+ * failed the screen in any stage of dg_step, and cells that went through the
+ * full limiter (equal without an indicator). */
+int dg_limiter_counts(dg_ctx* ctx, int64_t* queued, int64_t* full);
+
+/* One Adam step (bias-corrected, step >= 1) on FP32 params with moments m, v. */
+int dg_indicator_adam(float* params, float* m, float* v, const float* grads, int64_t n_params, float lr,
+                      float beta1, float beta2, float eps, int step, void* cuda_stream);
+
 /* ---- allocation-free entry point (no counterpart in the paper) ---------
  * R(y) exactly as dg_rhs computes it (same kernels; no driving source), for
  * callers that must not allocate device memory themselves: code whose device

@@ -62,6 +62,17 @@ _SIGS = {
     "dg_probe_fma_peak": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
     "dg_rhs_noalloc": (C.c_int, [C.POINTER(dg_mesh), C.c_int, C.c_double, C.c_int, C.c_void_p, C.c_void_p,
                                  C.c_void_p]),
+    "dg_indicator_sizes": (C.c_int, [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_size_t),
+                                     C.POINTER(C.c_size_t)]),
+    "dg_indicator_features": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "dg_indicator_forward": (C.c_int, [C.c_int, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "dg_indicator_backward": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_int64, C.c_float, C.c_void_p,
+                                        C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
+    "dg_indicator_adam": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_float,
+                                    C.c_float, C.c_float, C.c_float, C.c_int, C.c_void_p]),
+    "dg_set_indicator": (C.c_int, [C.c_void_p, C.c_void_p, C.c_float]),
+    "dg_indicator_capture": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "dg_limiter_counts": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
 }
 
 DG_KCLASS_COUNT = 6
@@ -226,6 +237,51 @@ def dg_rhs_noalloc(n, order, gamma, precision, y_dev, R_dev, stream, length=(1.0
         m.length[a] = float(length[a])
     _check(load().dg_rhs_noalloc(C.byref(m), int(order), float(gamma), int(precision), _ptr(y_dev), _ptr(R_dev),
                                  _ptr(stream)), "dg_rhs_noalloc")
+
+
+def dg_indicator_sizes(order):
+    """(n_features, n_padded, n_params, work_bytes)"""
+    a, b, c, d = C.c_int(0), C.c_int(0), C.c_size_t(0), C.c_size_t(0)
+    _check(load().dg_indicator_sizes(int(order), C.byref(a), C.byref(b), C.byref(c), C.byref(d)),
+           "dg_indicator_sizes")
+    return a.value, b.value, c.value, d.value
+
+
+def dg_indicator_features(ctx, y_dev, X_dev):
+    _check(load().dg_indicator_features(ctx, _ptr(y_dev), _ptr(X_dev)), "dg_indicator_features")
+
+
+def dg_indicator_forward(order, X_dev, n, params_dev, logits_dev, stream):
+    _check(load().dg_indicator_forward(int(order), _ptr(X_dev), int(n), _ptr(params_dev), _ptr(logits_dev),
+                                       _ptr(stream)), "dg_indicator_forward")
+
+
+def dg_indicator_backward(order, X_dev, labels_dev, n, pos_weight, params_dev, grads_dev, work_dev, work_bytes,
+                          stream):
+    _check(load().dg_indicator_backward(int(order), _ptr(X_dev), _ptr(labels_dev), int(n), float(pos_weight),
+                                        _ptr(params_dev), _ptr(grads_dev), _ptr(work_dev), int(work_bytes),
+                                        _ptr(stream)), "dg_indicator_backward")
+
+
+def dg_indicator_adam(params, m, v, grads, n_params, lr, beta1, beta2, eps, step, stream):
+    _check(load().dg_indicator_adam(_ptr(params), _ptr(m), _ptr(v), _ptr(grads), int(n_params), float(lr),
+                                    float(beta1), float(beta2), float(eps), int(step), _ptr(stream)),
+           "dg_indicator_adam")
+
+
+def dg_set_indicator(ctx, params_dev, threshold=0.5):
+    _check(load().dg_set_indicator(ctx, _ptr(params_dev), float(threshold)), "dg_set_indicator")
+
+
+def dg_indicator_capture(ctx, dt, X_dev, flags_dev, screen_dev):
+    _check(load().dg_indicator_capture(ctx, float(dt), _ptr(X_dev), _ptr(flags_dev), _ptr(screen_dev)),
+           "dg_indicator_capture")
+
+
+def dg_limiter_counts(ctx):
+    q, f = C.c_int64(0), C.c_int64(0)
+    _check(load().dg_limiter_counts(ctx, C.byref(q), C.byref(f)), "dg_limiter_counts")
+    return q.value, f.value
 
 
 def dg_probe_fma_peak(fp64):

@@ -12,6 +12,7 @@
 
 #include "dg.h"
 #include "dg_launch.h"
+#include "dg_mlp.h"
 
 using namespace dg;
 
@@ -159,6 +160,16 @@ void build_tables(double* t) {
           ++n;
         }
   }
+  for (int t2 = 0; t2 < Q; ++t2)
+    for (int t1 = 0; t1 < Q; ++t1) {
+      int j = 0;
+      for (int a = 0; a <= K; ++a)
+        for (int b = 0; a + b <= K; ++b) t[TB::F2D + (t1 + Q * t2) * TB::T + j++] = pt(a, g[t1]) * pt(b, g[t2]);
+    }
+  for (int e = 0; e <= K; ++e) {
+    t[TB::FEND + e] = pt(e, -1.0);
+    t[TB::FEND + (K + 1) + e] = pt(e, 1.0);
+  }
   for (int a = 0; a < Q; ++a) {
     t[TB::GX + a] = g[a];
     t[TB::GW + a] = gw[a];
@@ -231,6 +242,13 @@ __global__ void state_to_canon_kernel(const double* __restrict__ in, double* __r
   }
 }
 
+// out = y - dt * r (one forward-Euler stage, capture of training data)
+__global__ void euler_stage_kernel(const double* __restrict__ y, const double* __restrict__ r, double dt,
+                                   double* __restrict__ out, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = y[i] - dt * r[i];
+}
+
 constexpr int kRedBlocks = 1024;
 
 // part[i * gridDim.x + b] = sum of the cell means of variable i over block b's
@@ -295,6 +313,11 @@ struct dg_ctx {
   double* modes_dev = nullptr;
   double* sums = nullptr;  // 8 doubles
   double* ybuf = nullptr;
+  int* list = nullptr;
+  int* list2 = nullptr;
+  // learned indicator gate (caller-owned FP32 parameters)
+  const float* ind_params = nullptr;
+  float ind_logit_thr = 0.f;
   void* fh = nullptr;
   void* field = nullptr;
   // measurement: launch counts per kernel class, optional event timing
@@ -316,7 +339,7 @@ struct dg_ctx {
 namespace {
 
 struct Layout {
-  size_t ctrl, part, modes, sums, ybuf, fh, field, base_end, full_end;
+  size_t ctrl, part, modes, sums, ybuf, list, list2, fh, field, base_end, full_end;
 };
 
 Layout layout_of(const dg_ctx* c) {
@@ -334,6 +357,10 @@ Layout layout_of(const dg_ctx* c) {
   o += align256(sizeof(double) * 8);
   L.ybuf = o;
   o += align256(sizeof(double) * 5 * c->N * nc);
+  L.list = o;
+  o += align256(sizeof(int) * nc);
+  L.list2 = o;
+  o += align256(sizeof(int) * nc);
   L.fh = o;
   o += align256(sizeof(double) * 15 * c->Q * c->Q * nc);
   L.base_end = o;
@@ -529,6 +556,9 @@ int dg_bind(dg_ctx* c, double* y_dev, void* scratch_dev, size_t scratch_bytes, v
   c->modes_dev = reinterpret_cast<double*>(c->scratch + L.modes);
   c->sums = reinterpret_cast<double*>(c->scratch + L.sums);
   c->ybuf = reinterpret_cast<double*>(c->scratch + L.ybuf);
+  c->list = reinterpret_cast<int*>(c->scratch + L.list);
+  c->list2 = reinterpret_cast<int*>(c->scratch + L.list2);
+  c->ind_params = nullptr;
   c->fh = c->scratch + L.fh;
   c->field = c->forcing_capable ? c->scratch + L.field : nullptr;
   c->bound = true;
@@ -634,10 +664,27 @@ int dg_step(dg_ctx* c, double dt) {
   for (int s = 0; s < 3; ++s) {
     double* out = s < 2 ? c->ybuf : c->y;
     DG_TRY(launch(c, KC_FACE, [&] { return c->fn.face(c->prec, ys, c->fh, c->geo, c->stream); }));
+    DG_CUDA(cudaMemsetAsync(&c->ctrl->n_flag, 0, sizeof(unsigned), c->stream));
     DG_TRY(launch(c, KC_VOLUME, [&] {
-      return c->fn.volume_stage(c->prec, force, c->fh, c->field, c->geo, ys, c->y, out, a0[s], b0[s], dt, c->ctrl,
-                                c->stream);
+      return c->fn.volume_stage(c->prec, force, c->fh, c->field, c->geo, ys, c->y, out, a0[s], b0[s], dt, c->list,
+                                c->ctrl, c->stream);
     }));
+    // the limiter of the next stage's input: cells that failed the screen,
+    // filtered by the learned indicator when one is set
+    if (c->ind_params) {
+      DG_CUDA(cudaMemsetAsync(&c->ctrl->n_gate, 0, sizeof(unsigned), c->stream));
+      DG_TRY(launch(c, KC_LIMIT, [&] {
+        return dg::mlp::gate_for(c->k, out, c->geo, c->list, &c->ctrl->n_flag, c->ind_params, c->ind_logit_thr,
+                                 c->list2, &c->ctrl->n_gate, &c->ctrl->n_queued_total, c->stream);
+      }));
+      DG_TRY(launch(c, KC_LIMIT, [&] {
+        return c->fn.limit_list(out, c->list2, &c->ctrl->n_gate, c->geo, c->ctrl, 0, c->stream);
+      }));
+    } else {
+      DG_TRY(launch(c, KC_LIMIT, [&] {
+        return c->fn.limit_list(out, c->list, &c->ctrl->n_flag, c->geo, c->ctrl, 1, c->stream);
+      }));
+    }
     ys = out;
   }
   c->limited = true;
@@ -728,8 +775,15 @@ int dg_energy_reset(dg_ctx* c, double c_iso, double rho0, double* dissipated) {
   DG_TRY(set_device(c));
   int n_part = 0;
   const double c2g = c_iso * c_iso / (c->geo.gamma - 1.0);
+  DG_CUDA(cudaMemsetAsync(&c->ctrl->n_flag, 0, sizeof(unsigned), c->stream));
   DG_TRY(launch(c, KC_RESET, [&] {
-    return c->fn.energy_reset(c->prec, c->y, c->geo, c2g, 1.0 / rho0, c->part, &n_part, c->ctrl, c->stream);
+    return c->fn.energy_reset(c->prec, c->y, c->geo, c2g, 1.0 / rho0, c->part, &n_part, c->list, c->ctrl,
+                              c->stream);
+  }));
+  // the positivity limiter after the reset (Sect. 3.2): full limiter on the
+  // cells that failed the screen
+  DG_TRY(launch(c, KC_RESET, [&] {
+    return c->fn.limit_list(c->y, c->list, &c->ctrl->n_flag, c->geo, c->ctrl, 0, c->stream);
   }));
   c->limited = true;
   if (dissipated) {
@@ -770,6 +824,58 @@ int dg_check(dg_ctx* c) {
   DG_TRY(need_bound(c));
   DG_TRY(set_device(c));
   return sync_and_check(c, nullptr);
+}
+
+int dg_set_indicator(dg_ctx* c, const float* params_dev, float threshold) {
+  if (!c) return DG_ERR_ARG;
+  if (!params_dev) {
+    c->ind_params = nullptr;
+    return DG_OK;
+  }
+  if (c->k < 1 || !(threshold > 0.f) || !(threshold < 1.f)) return DG_ERR_ARG;
+  c->ind_params = params_dev;
+  c->ind_logit_thr = std::log(threshold / (1.f - threshold));
+  return DG_OK;
+}
+
+int dg_indicator_capture(dg_ctx* c, double dt, uint16_t* X_dev, int8_t* flags_dev, uint8_t* screen_dev) {
+  DG_TRY(need_bound(c));
+  if (c->k < 1 || !(dt > 0.0) || !X_dev || !flags_dev || !screen_dev) return DG_ERR_ARG;
+  DG_TRY(set_device(c));
+  const bool force = c->n_force > 0;
+  const long long n = (long long)5 * c->N * c->geo.nc;
+  DG_TRY(launch(c, KC_FACE, [&] { return c->fn.face(c->prec, c->y, c->fh, c->geo, c->stream); }));
+  DG_TRY(launch(c, KC_VOLUME, [&] {
+    return c->fn.volume_rhs(c->prec, force, c->y, c->fh, c->field, c->geo, c->ybuf, c->ctrl, c->stream);
+  }));
+  DG_TRY(launch(c, KC_OTHER, [&] {
+    euler_stage_kernel<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(c->y, c->ybuf, dt, c->ybuf, n);
+    return cudaGetLastError();
+  }));
+  DG_TRY(launch(c, KC_OTHER, [&] { return dg::mlp::features_for(c->k, c->ybuf, c->geo, X_dev, c->stream); }));
+  DG_TRY(launch(c, KC_OTHER, [&] { return c->fn.screen(c->ybuf, screen_dev, c->geo, c->stream); }));
+  DG_TRY(launch(c, KC_LIMIT, [&] { return c->fn.limit(c->ybuf, flags_dev, c->geo, c->ctrl, c->stream); }));
+  return sync_and_check(c, nullptr);
+}
+
+int dg_limiter_counts(dg_ctx* c, int64_t* queued, int64_t* full) {
+  DG_TRY(need_bound(c));
+  DG_TRY(set_device(c));
+  Ctrl h{};
+  int st = sync_and_check(c, &h);
+  if (queued) *queued = (int64_t)h.n_queued_total;
+  if (full) *full = (int64_t)h.n_full_total;
+  DG_CUDA(cudaMemsetAsync(&c->ctrl->n_queued_total, 0, 2 * sizeof(unsigned long long), c->stream));
+  DG_CUDA(cudaStreamSynchronize(c->stream));
+  return st;
+}
+
+int dg_indicator_features(dg_ctx* c, const double* y_dev, uint16_t* X_dev) {
+  DG_TRY(need_bound(c));
+  if (!X_dev || c->k < 1) return DG_ERR_ARG;
+  DG_TRY(set_device(c));
+  const double* y = y_dev ? y_dev : c->y;
+  return launch(c, KC_OTHER, [&] { return dg::mlp::features_for(c->k, y, c->geo, X_dev, c->stream); });
 }
 
 int dg_set_timing(dg_ctx* c, int on) {

@@ -10,6 +10,14 @@ namespace dg {
 // ------------------------------------------------------------- sizes
 __host__ __device__ constexpr int nmodes(int k) { return (k + 1) * (k + 2) * (k + 3) / 6; }
 __host__ __device__ constexpr int gll_m(int k) { return k <= 1 ? 2 : 3; }
+// index of mode (u, v, w) in the exchange order (total degree ascending,
+// then u descending, then v descending)
+__host__ __device__ constexpr int mode_index(int u, int v, int w) {
+  const int D = u + v + w;
+  int idx = D > 0 ? nmodes(D - 1) : 0;
+  for (int up = D; up > u; --up) idx += D - up + 1;
+  return idx + (D - u - v);
+}
 
 // Per-degree basis/quadrature tables (Sect. 2.2-2.5), all values at the
 // method's point sets, offsets in elements. Weights are folded in so the
@@ -36,8 +44,14 @@ struct Tab {
   static constexpr int LPHI = FPHIW + 6 * Q2 * N;
   // max over S of |phi_l|, [N]
   static constexpr int LMAX = LPHI + NL * N;
+  // tangential products Pt_a(x_t1) Pt_b(x_t2) at the face points, pairs
+  // (a, b) with a + b <= K in the order a ascending, b ascending, [Q2][T]
+  static constexpr int T = (K + 1) * (K + 2) / 2;
+  static constexpr int F2D = LMAX + N;
+  // Pt_e(-1) and Pt_e(+1), [2][K+1]
+  static constexpr int FEND = F2D + Q2 * T;
   // 1D Gauss nodes and weights, [Q] each
-  static constexpr int GX = LMAX + N;
+  static constexpr int GX = FEND + 2 * (K + 1);
   static constexpr int GW = GX + Q;
   static constexpr int SIZE = GW + Q;
 };
@@ -55,9 +69,13 @@ enum : unsigned {
 struct Ctrl {
   unsigned long long cfl_max_bits;  // max over cells of the wave-speed sum (bits of a double >= 0)
   unsigned int err;                 // sticky ERRB_* bits
-  unsigned int pad0;
+  unsigned int n_flag;              // cells queued for the full limiter
   unsigned long long n_limited;     // limiter count
-  double pad1[5];
+  unsigned int n_gate;              // queued cells the indicator passes on
+  unsigned int pad2;
+  unsigned long long n_queued_total;  // cells that failed the limiter screen (all stages)
+  unsigned long long n_full_total;    // cells that went through the full limiter
+  double pad1[2];
 };
 
 struct Geo {
@@ -100,7 +118,16 @@ __device__ __forceinline__ void hllc_flux(int d, const T* UL, const T* UR, T gam
   T vR[3] = {UR[1] * irR, UR[2] * irR, UR[3] * irR};
   T pL = gm1 * (UL[4] - T(0.5) * UL[0] * (vL[0] * vL[0] + vL[1] * vL[1] + vL[2] * vL[2]));
   T pR = gm1 * (UR[4] - T(0.5) * UR[0] * (vR[0] * vR[0] + vR[1] * vR[1] + vR[2] * vR[2]));
-  T cL = sqrt(gamma * pL * irL), cR = sqrt(gamma * pR * irR);
+  T cL, cR;
+  if constexpr (sizeof(T) == 4) {
+    // FP32 traces of a state limited in FP64 can round a pressure near the
+    // floor below zero: clamp the squared sound speeds
+    cL = sqrt(fmaxf(gamma * pL * irL, 0.f));
+    cR = sqrt(fmaxf(gamma * pR * irR, 0.f));
+  } else {
+    cL = sqrt(gamma * pL * irL);
+    cR = sqrt(gamma * pR * irR);
+  }
   T sL = sqrt(UL[0]), sR = sqrt(UR[0]);
   T iss = T(1) / (sL + sR);
   T vt[3], v2 = T(0);

@@ -44,11 +44,20 @@ cudaError_t set_volume_smem() {
                               (int)VolCfg<KK, T>::smem(FORCE));
 }
 
+constexpr bool kRegF32 = KK <= 2;
+
+template <int MODE, bool FORCE>
+cudaError_t set_f32_smem_fw() {
+  return cudaFuncSetAttribute(volume_f32_kernel<KK, MODE, FORCE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)VolF32<KK>::smem(FORCE));
+}
+
 cudaError_t upload(const double* h64, const float* h32) {
   cudaError_t e = cudaMemcpyToSymbol(g_tab64, h64, sizeof(double) * TB::SIZE);
   if (e != cudaSuccess) return e;
   e = cudaMemcpyToSymbol(g_tab32, h32, sizeof(float) * TB::SIZE);
   if (e != cudaSuccess) return e;
+  if ((e = cudaMemcpyToSymbol(c_tab32, h32, sizeof(float) * TB::SIZE)) != cudaSuccess) return e;
   void* p = nullptr;
   const int dev = cur_dev();
   if ((e = cudaGetSymbolAddress(&p, g_tab64)) != cudaSuccess) return e;
@@ -56,6 +65,12 @@ cudaError_t upload(const double* h64, const float* h32) {
   if ((e = cudaGetSymbolAddress(&p, g_tab32)) != cudaSuccess) return e;
   h_tab32[dev] = static_cast<const float*>(p);
   cudaError_t r = cudaSuccess;
+  if constexpr (kRegF32) {
+    cudaError_t f[4] = {set_f32_smem_fw<MODE_RHS, false>(), set_f32_smem_fw<MODE_RHS, true>(),
+                        set_f32_smem_fw<MODE_STAGE, false>(), set_f32_smem_fw<MODE_STAGE, true>()};
+    for (cudaError_t x : f)
+      if (x != cudaSuccess) r = x;
+  }
   cudaError_t s[8] = {set_volume_smem<double, MODE_RHS, false>(),  set_volume_smem<double, MODE_RHS, true>(),
                       set_volume_smem<double, MODE_STAGE, false>(), set_volume_smem<double, MODE_STAGE, true>(),
                       set_volume_smem<float, MODE_RHS, false>(),   set_volume_smem<float, MODE_RHS, true>(),
@@ -67,13 +82,31 @@ cudaError_t upload(const double* h64, const float* h32) {
 
 template <typename T>
 cudaError_t face_t(const double* y, void* fh, const Geo& g, cudaStream_t s) {
-  dim3 grid(grid1(g.nc, kThreads), TB::Q2, 3);
-  face_flux_kernel<KK, T><<<grid, kThreads, 0, s>>>(y, static_cast<T*>(fh), tab_ptr<T>(), g);
+  dim3 grid(grid1(g.nc, 32), 3);
+  face_flux_kernel<KK, T><<<grid, dim3(32, TB::Q2), 0, s>>>(y, static_cast<T*>(fh), tab_ptr<T>(), g);
   return cudaGetLastError();
 }
 
+// FP32 tiled kernels with constant-bank tables for degrees <= 2; degree 3
+// keeps the generic shared-memory kernels.
+
 cudaError_t face(int prec, const double* y, void* fh, const Geo& g, cudaStream_t s) {
+  if constexpr (kRegF32) {
+    if (prec) {
+      face_flux_f32_kernel<KK><<<grid1(g.nc, 32), 96, 0, s>>>(y, static_cast<float*>(fh), g);
+      return cudaGetLastError();
+    }
+  }
   return prec ? face_t<float>(y, fh, g, s) : face_t<double>(y, fh, g, s);
+}
+
+template <int MODE, bool FORCE>
+cudaError_t vol_f32(const double* y, const void* fh, const void* field, const Geo& g, StageArgs st, double* R,
+                    Ctrl* ctrl, cudaStream_t s) {
+  using CF = VolF32<KK>;
+  volume_f32_kernel<KK, MODE, FORCE><<<grid1(g.nc, CF::C), CF::THREADS, CF::smem(FORCE), s>>>(
+      y, static_cast<const float*>(fh), static_cast<const float*>(field), tab_ptr<double>(), g, st, R, ctrl);
+  return cudaGetLastError();
 }
 
 template <typename T, int MODE, bool FORCE>
@@ -88,6 +121,11 @@ cudaError_t vol_t(const double* y, const void* fh, const void* field, const Geo&
 cudaError_t volume_rhs(int prec, bool force, const double* y, const void* fh, const void* field, const Geo& g,
                        double* R, Ctrl* ctrl, cudaStream_t s) {
   StageArgs st{};
+  if constexpr (kRegF32) {
+    if (prec)
+      return force ? vol_f32<MODE_RHS, true>(y, fh, field, g, st, R, ctrl, s)
+                   : vol_f32<MODE_RHS, false>(y, fh, field, g, st, R, ctrl, s);
+  }
   if (prec)
     return force ? vol_t<float, MODE_RHS, true>(y, fh, field, g, st, R, ctrl, s)
                  : vol_t<float, MODE_RHS, false>(y, fh, field, g, st, R, ctrl, s);
@@ -96,14 +134,30 @@ cudaError_t volume_rhs(int prec, bool force, const double* y, const void* fh, co
 }
 
 cudaError_t volume_stage(int prec, bool force, const void* fh, const void* field, const Geo& g, const double* ys,
-                         const double* y0, double* out, double a0, double b0, double dt, Ctrl* ctrl,
+                         const double* y0, double* out, double a0, double b0, double dt, int* list, Ctrl* ctrl,
                          cudaStream_t s) {
-  StageArgs st{ys, y0, out, a0, b0, dt};
+  StageArgs st{ys, y0, out, a0, b0, dt, list};
+  if constexpr (kRegF32) {
+    if (prec)
+      return force ? vol_f32<MODE_STAGE, true>(ys, fh, field, g, st, nullptr, ctrl, s)
+                   : vol_f32<MODE_STAGE, false>(ys, fh, field, g, st, nullptr, ctrl, s);
+  }
   if (prec)
     return force ? vol_t<float, MODE_STAGE, true>(ys, fh, field, g, st, nullptr, ctrl, s)
                  : vol_t<float, MODE_STAGE, false>(ys, fh, field, g, st, nullptr, ctrl, s);
   return force ? vol_t<double, MODE_STAGE, true>(ys, fh, field, g, st, nullptr, ctrl, s)
                : vol_t<double, MODE_STAGE, false>(ys, fh, field, g, st, nullptr, ctrl, s);
+}
+
+cudaError_t limit_list(double* y, const int* list, const unsigned* count, const Geo& g, Ctrl* ctrl, int count_queued,
+                       cudaStream_t s) {
+  limit_list_kernel<KK><<<152, kThreads, 0, s>>>(y, list, count, tab_ptr<double>(), g, ctrl, count_queued);
+  return cudaGetLastError();
+}
+
+cudaError_t screen(const double* y, uint8_t* scr, const Geo& g, cudaStream_t s) {
+  screen_kernel<KK><<<grid1(g.nc, kThreads), kThreads, 0, s>>>(y, scr, tab_ptr<double>(), g);
+  return cudaGetLastError();
 }
 
 cudaError_t limit(double* y, int8_t* flags, const Geo& g, Ctrl* ctrl, cudaStream_t s) {
@@ -118,22 +172,22 @@ cudaError_t cfl(const double* y, const Geo& g, Ctrl* ctrl, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-constexpr int kResetCells = KK >= 3 ? 16 : 32;
+constexpr int kResetCells = 32;
 
 template <typename T>
-cudaError_t reset_t(double* y, const Geo& g, double c2g, double inv_rho0, double* part, int* n_part, Ctrl* ctrl,
-                    cudaStream_t s) {
+cudaError_t reset_t(double* y, const Geo& g, double c2g, double inv_rho0, double* part, int* n_part, int* list,
+                    Ctrl* ctrl, cudaStream_t s) {
   unsigned nb = grid1(g.nc, kResetCells);
   *n_part = (int)nb;
-  energy_reset_kernel<KK, T, kResetCells><<<nb, kThreads, 0, s>>>(y, tab_ptr<T>(), tab_ptr<double>(), g, c2g, inv_rho0, part,
-                                                                  ctrl);
+  energy_reset_kernel<KK, T, kResetCells><<<nb, kThreads, 0, s>>>(y, tab_ptr<T>(), tab_ptr<double>(), g, c2g, inv_rho0,
+                                                                  part, list, ctrl);
   return cudaGetLastError();
 }
 
 cudaError_t energy_reset(int prec, double* y, const Geo& g, double c2g, double inv_rho0, double* part, int* n_part,
-                         Ctrl* ctrl, cudaStream_t s) {
-  return prec ? reset_t<float>(y, g, c2g, inv_rho0, part, n_part, ctrl, s)
-              : reset_t<double>(y, g, c2g, inv_rho0, part, n_part, ctrl, s);
+                         int* list, Ctrl* ctrl, cudaStream_t s) {
+  return prec ? reset_t<float>(y, g, c2g, inv_rho0, part, n_part, list, ctrl, s)
+              : reset_t<double>(y, g, c2g, inv_rho0, part, n_part, list, ctrl, s);
 }
 
 cudaError_t project(const double* f, double* y, const Geo& g, cudaStream_t s) {
@@ -166,6 +220,8 @@ Launchers DG_PASTE(launchers_k, DG_K)() {
   L.volume_rhs = volume_rhs;
   L.volume_stage = volume_stage;
   L.limit = limit;
+  L.limit_list = limit_list;
+  L.screen = screen;
   L.cfl = cfl;
   L.energy_reset = energy_reset;
   L.project = project;

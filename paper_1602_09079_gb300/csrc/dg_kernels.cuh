@@ -42,6 +42,7 @@ struct StageArgs {
   const double* y0;  // y^(0) of the step
   double* out;       // stage output (may alias ys or y0; cells are CTA-private)
   double a0, b0, dt; // out = a0 y0 + b0 (ys - dt R(ys))
+  int* list;         // cells whose limiter screen failed (FP32 register path)
 };
 
 __device__ __forceinline__ void cell_xyz(long long c, const Geo& g, int& ix, int& iy, int& iz) {
@@ -60,18 +61,20 @@ __device__ __forceinline__ long long neighbour(const Geo& g, int ix, int iy, int
 }
 
 // ------------------------------------------------------------ face fluxes
-// grid: x over cells, y = face point p in [0, Q^2), z = direction d.
+// block: 32 consecutive cells x the Q^2 face points (threadIdx.y), so the
+// warps of one block share the two cells' coefficients through L1;
+// grid: x over cell groups, y = direction d.
 // Face (d, c) joins the lower cell c - e_d (left state, its high face) and
 // cell c (right state, its low face). fh[((d*5 + i)*Q2 + p)*nc + c].
 template <int K, typename T>
-__global__ void __launch_bounds__(kThreads) face_flux_kernel(const double* __restrict__ y, T* __restrict__ fh,
-                                                             const T* __restrict__ tab, Geo g) {
+__global__ void __launch_bounds__(512) face_flux_kernel(const double* __restrict__ y, T* __restrict__ fh,
+                                                        const T* __restrict__ tab, Geo g) {
   using TB = Tab<K>;
   constexpr int N = TB::N, Q2 = TB::Q2;
   const long long nc = g.nc;
-  const long long c = (long long)blockIdx.x * kThreads + threadIdx.x;
+  const long long c = (long long)blockIdx.x * 32 + threadIdx.x;
   if (c >= nc) return;
-  const int p = blockIdx.y, d = blockIdx.z;
+  const int p = threadIdx.y, d = blockIdx.y;
   int ix, iy, iz;
   cell_xyz(c, g, ix, iy, iz);
   const long long cl = neighbour(g, ix, iy, iz, d, -1);
@@ -96,6 +99,32 @@ __global__ void __launch_bounds__(kThreads) face_flux_kernel(const double* __res
   for (int i = 0; i < 5; ++i) fh[((size_t)(d * 5 + i) * Q2 + p) * nc + c] = F[i];
 }
 
+// Screen of the positivity limiter from a cell's FP64 means and the sums
+// sabs_i = sum_{l>=1} |w_il| max_S |phi_l| (same test and margins as
+// limit_cell): true when the cell provably needs no limiting.
+template <int K>
+__device__ __forceinline__ bool limiter_screen(const double* mean, const double* sabs, bool finite, double gamma,
+                                               double eps_r, double eps_p) {
+  if (!finite) return false;
+  const double gm1 = gamma - 1.0;
+  const double r = mean[0];
+  const double pbar = gm1 * (mean[4] - 0.5 * (mean[1] * mean[1] + mean[2] * mean[2] + mean[3] * mean[3]) / r);
+  if (!(r >= eps_r) || !(pbar >= eps_p)) return false;
+  if (nmodes(K) == 1) return true;
+  const double rlo = r - sabs[0];
+  if (!(rlo >= eps_r + 1e-13 * (fabs(r) + sabs[0]))) return false;
+  const double elo = mean[4] - sabs[4];
+  double kin = 0.0;
+#pragma unroll
+  for (int a = 1; a <= 3; ++a) {
+    const double mh = fabs(mean[a]) + sabs[a];
+    kin += mh * mh;
+  }
+  kin *= 0.5 / rlo;
+  const double plo = gm1 * (elo - kin);
+  return plo >= eps_p + 1e-13 * gm1 * (fabs(mean[4]) + sabs[4] + kin);
+}
+
 // --------------------------------------------------------------- volume
 template <int K, typename T, int MODE, bool FORCE>
 __global__ void __launch_bounds__(kThreads) volume_kernel(const double* __restrict__ yin, const T* __restrict__ fh,
@@ -110,12 +139,9 @@ __global__ void __launch_bounds__(kThreads) volume_kernel(const double* __restri
   T* sW = reinterpret_cast<T*>(sY + 5 * N * C);
   T* sF = sW + 5 * N * C;
   T* sS = sF + 15 * Q3 * C;
-  __shared__ unsigned s_err;
-
   const long long nc = g.nc;
   const long long c0 = (long long)blockIdx.x * C;
   const int tid = threadIdx.x;
-  if (tid == 0) s_err = 0u;
   const double* ysrc = (MODE == MODE_STAGE) ? st.ys : yin;
 
   // phase 1: stage input -> shared (converted to T), coalesced rows
@@ -220,22 +246,374 @@ __global__ void __launch_bounds__(kThreads) volume_kernel(const double* __restri
   if (MODE == MODE_RHS) return;
   __syncthreads();
 
-  // phase 4: positivity limiter of the next stage's input (FP64)
-  if (tid < C) {
-    const long long cell = c0 + tid;
-    if (cell < nc) {
-      unsigned e = 0;
-      limit_cell<K>(sY + tid, C, tab64, g.gamma, g.eps_rho, g.eps_p, &e);
-      if (e) atomicOr(&s_err, e);
-    }
-  }
-  __syncthreads();
+  // phase 4: limiter screen of the next stage's input (FP64); cells that
+  // fail it are queued for the full limiter
   for (int it = tid; it < 5 * N * C; it += kThreads) {
     const int c = it % C, r = it / C;
     const long long cell = c0 + c;
     if (cell < nc) st.out[(size_t)r * nc + cell] = sY[r * C + c];
   }
-  if (tid == 0 && s_err) atomicOr(&ctrl->err, s_err);
+  if (tid < C) {
+    const long long cell = c0 + tid;
+    if (cell < nc) {
+      double m[5], a[5];
+      bool fin = true;
+#pragma unroll
+      for (int i = 0; i < 5; ++i) {
+        m[i] = sY[(i * N) * C + tid];
+        double sa = 0.0;
+        for (int l = 1; l < N; ++l) sa += fabs(sY[(i * N + l) * C + tid]) * __ldg(tab64 + TB::LMAX + l);
+        a[i] = sa;
+        for (int l = 0; l < N; ++l) fin &= isfinite(sY[(i * N + l) * C + tid]);
+      }
+      if (!limiter_screen<K>(m, a, fin, g.gamma, g.eps_rho, g.eps_p)) {
+        const unsigned slot = atomicAdd(&ctrl->n_flag, 1u);
+        st.list[slot] = (int)cell;
+      }
+    }
+  }
+}
+
+// ============================================================ FP32 path
+
+// FP32 copy of this degree's tables in constant memory: with the point and
+// mode loops unrolled, every table value is a compile-time offset into the
+// constant bank and becomes an FMA operand (no load instruction).
+namespace {
+__constant__ float c_tab32[Tab<3>::SIZE];
+}
+
+// Face fluxes, FP32: tiles of 32 consecutive cells, warp d computes the low
+// face in direction d of each cell (left state = the lower neighbour's high
+// face, right state = the cell's own low face). Traces are sum-factorised:
+// the coefficients are first contracted with Pt_e(+-1) along the normal into
+// the tangential coefficients E[i][(a,b)], which then give the values at all
+// Q^2 face points through the tangential products (constant tables).
+template <int K, int D>
+__device__ __forceinline__ void face_f32_dir(const double* __restrict__ y, float* __restrict__ fh, const Geo& g,
+                                             long long c, int ix, int iy, int iz) {
+  using TB = Tab<K>;
+  constexpr int N = TB::N, Q2 = TB::Q2, T = TB::T;
+  const long long nc = g.nc;
+  const long long cl = neighbour(g, ix, iy, iz, D, -1);
+  float EL[5 * T], ER[5 * T];
+#pragma unroll
+  for (int j = 0; j < 5 * T; ++j) {
+    EL[j] = 0.f;
+    ER[j] = 0.f;
+  }
+  // exponents along (normal, tangential 1, tangential 2) -> (u, v, w)
+#pragma unroll
+  for (int a = 0, j = 0; a <= K; ++a)
+#pragma unroll
+    for (int b = 0; a + b <= K; ++b, ++j)
+#pragma unroll
+      for (int e = 0; e + a + b <= K; ++e) {
+        const int m = D == 0 ? mode_index(e, a, b) : (D == 1 ? mode_index(a, e, b) : mode_index(a, b, e));
+        const float pl = c_tab32[TB::FEND + (K + 1) + e];  // lower cell: its high face, xi_d = +1
+        const float pr = c_tab32[TB::FEND + e];            // own cell: its low face, xi_d = -1
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+          EL[i * T + j] += (float)__ldg(y + (size_t)(i * N + m) * nc + cl) * pl;
+          ER[i * T + j] += (float)__ldg(y + (size_t)(i * N + m) * nc + c) * pr;
+        }
+      }
+  const float gamma = (float)g.gamma;
+#pragma unroll 1
+  for (int p = 0; p < Q2; ++p) {
+    float UL[5], UR[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      float aL = 0.f, aR = 0.f;
+#pragma unroll
+      for (int j = 0; j < T; ++j) {
+        const float t2 = c_tab32[TB::F2D + p * T + j];
+        aL += EL[i * T + j] * t2;
+        aR += ER[i * T + j] * t2;
+      }
+      UL[i] = aL;
+      UR[i] = aR;
+    }
+    float F[5];
+    hllc_flux<float>(D, UL, UR, gamma, F);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) fh[((size_t)(D * 5 + i) * Q2 + p) * nc + c] = F[i];
+  }
+}
+
+template <int K>
+__global__ void __launch_bounds__(96, 6) face_flux_f32_kernel(const double* __restrict__ y, float* __restrict__ fh,
+                                                           Geo g) {
+  const long long c = (long long)blockIdx.x * 32 + (threadIdx.x & 31);
+  if (c >= g.nc) return;
+  const int d = threadIdx.x >> 5;  // warp-uniform direction
+  int ix, iy, iz;
+  cell_xyz(c, g, ix, iy, iz);
+  if (d == 0) face_f32_dir<K, 0>(y, fh, g, c, ix, iy, iz);
+  else if (d == 1) face_f32_dir<K, 1>(y, fh, g, c, ix, iy, iz);
+  else face_f32_dir<K, 2>(y, fh, g, c, ix, iy, iz);
+}
+
+// Volume quadrature, FP32, tiled in two phases over a tile of C cells:
+//  A) one warp per group of PG volume points (warp-uniform group, so the
+//     point loop unrolls against compile-time constant-table offsets): the
+//     cell's coefficients in registers, values at the points, Euler fluxes
+//     (and the driving source) to shared memory;
+//  B) one warp per conserved variable: the N accumulators of one (cell,
+//     variable) in registers, the flux projection onto the basis gradients,
+//     the source projection and the six face fluxes projected onto the face
+//     traces, every table value a constant-bank operand; then R, or the FP64
+//     SSP-RK3 stage combination and the limiter screen (cells failing it are
+//     queued for the full limiter).
+template <int K>
+struct VolF32 {
+  static constexpr int Q3 = (K + 1) * (K + 1) * (K + 1);
+  static constexpr int N = nmodes(K);
+  static constexpr int C = K >= 2 ? 32 : 64;  // cells per tile (a multiple of 32)
+  static constexpr int NW = K >= 2 ? 3 : (K == 1 ? 2 : 1);  // warps of phase A (point subgroups)
+  static constexpr int NCH = K >= 2 ? 3 : 1;                // point chunks (phase A/B rounds)
+  static constexpr int PC = Q3 / NCH;                       // points per chunk
+  static constexpr int PW = PC / NW;                        // points per phase-A warp and chunk
+  static constexpr int THREADS = 5 * C;
+  static constexpr int MINB = K >= 2 ? 4 : 3;  // CTAs per SM the register budget is sized for
+  static constexpr size_t smem(bool force) {
+    return sizeof(float) * (size_t)(5 * N * C + 15 * PC * C + (force ? 4 * PC * C : 0)) +
+           sizeof(double) * (size_t)(10 * C);
+  }
+  static_assert(K > 2 || (Q3 % NCH == 0 && PC % NW == 0), "point chunks");
+};
+
+// phase A of one chunk for one warp: points q = CH*PC + W*PW + j
+template <int K, int CH, int W, bool FORCE>
+__device__ __forceinline__ void vol_f32_points(const float* sW, float* sF, float* sS, const float* __restrict__ field,
+                                               int c, long long cell, long long nc, float gm1, const float* idx) {
+  using TB = Tab<K>;
+  using CF = VolF32<K>;
+  constexpr int N = TB::N, Q3 = TB::Q3, C = CF::C, PC = CF::PC;
+  float w[5 * N];
+#pragma unroll
+  for (int r = 0; r < 5 * N; ++r) w[r] = sW[r * C + c];
+#pragma unroll
+  for (int j = 0; j < CF::PW; ++j) {
+    const int ql = W * CF::PW + j;  // point within the chunk
+    const int q = CH * PC + ql;
+    float U[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      float a = 0.f;
+#pragma unroll
+      for (int l = 0; l < N; ++l) a += w[i * N + l] * c_tab32[TB::VPHI + q * N + l];
+      U[i] = a;
+    }
+    const float ir = 1.f / U[0];
+    const float v[3] = {U[1] * ir, U[2] * ir, U[3] * ir};
+    const float p = gm1 * (U[4] - 0.5f * U[0] * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]));
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      float F[5];
+      euler_flux<float>(d, U, v, p, F);
+#pragma unroll
+      for (int i = 0; i < 5; ++i) sF[((d * 5 + i) * PC + ql) * C + c] = F[i] * idx[d];
+    }
+    if (FORCE) {
+      float a[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) a[d] = __ldg(field + ((size_t)d * Q3 + q) * nc + cell);
+      sS[(0 * PC + ql) * C + c] = U[0] * a[0];
+      sS[(1 * PC + ql) * C + c] = U[0] * a[1];
+      sS[(2 * PC + ql) * C + c] = U[0] * a[2];
+      sS[(3 * PC + ql) * C + c] = U[1] * a[0] + U[2] * a[1] + U[3] * a[2];
+    }
+  }
+}
+
+// phase B of one chunk: accumulate the projections of its points
+template <int K, int CH, bool FORCE>
+__device__ __forceinline__ void vol_f32_project(const float* sF, const float* sS, int c, int i, float (&acc)[nmodes(K)]) {
+  using TB = Tab<K>;
+  using CF = VolF32<K>;
+  constexpr int N = TB::N, Q3 = TB::Q3, C = CF::C, PC = CF::PC;
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+#pragma unroll
+    for (int ql = 0; ql < PC; ++ql) {
+      const int q = CH * PC + ql;
+      const float f = sF[((d * 5 + i) * PC + ql) * C + c];
+#pragma unroll
+      for (int l = 0; l < N; ++l) acc[l] += f * c_tab32[TB::VDPHI + (d * Q3 + q) * N + l];
+    }
+  if (FORCE && i > 0) {
+#pragma unroll
+    for (int ql = 0; ql < PC; ++ql) {
+      const int q = CH * PC + ql;
+      const float sv = sS[((i - 1) * PC + ql) * C + c];
+#pragma unroll
+      for (int l = 0; l < N; ++l) acc[l] += sv * c_tab32[TB::VPHIW + q * N + l];
+    }
+  }
+}
+
+template <int K, int CH, bool FORCE>
+__device__ __forceinline__ void vol_f32_chunk(const float* sW, float* sF, float* sS, const float* __restrict__ field,
+                                              long long c0, long long nc, float gm1, const float* idx,
+                                              float (&acc)[nmodes(K)]) {
+  using CF = VolF32<K>;
+  constexpr int C = CF::C;
+  const int tid = threadIdx.x;
+  {
+    const int c = tid % C, wg = tid / C;  // warp-uniform phase-A role
+    const long long cell = c0 + c;
+    const long long cellc = cell < nc ? cell : nc - 1;  // ragged tail: in-bounds field reads
+    if (wg == 0) vol_f32_points<K, CH, 0, FORCE>(sW, sF, sS, field, c, cellc, nc, gm1, idx);
+    if (CF::NW > 1 && wg == 1) vol_f32_points<K, CH, (CF::NW > 1 ? 1 : 0), FORCE>(sW, sF, sS, field, c, cellc, nc, gm1, idx);
+    if (CF::NW > 2 && wg == 2) vol_f32_points<K, CH, (CF::NW > 2 ? 2 : 0), FORCE>(sW, sF, sS, field, c, cellc, nc, gm1, idx);
+  }
+  __syncthreads();
+  vol_f32_project<K, CH, FORCE>(sF, sS, tid % C, tid / C, acc);
+  __syncthreads();
+}
+
+// Volume quadrature, FP32, over a tile of C cells in NCH chunks of points:
+//  A) NW warps, each on a fixed subgroup of the chunk's points (warp-uniform,
+//     so the point loop unrolls against compile-time constant-table offsets):
+//     the cell's coefficients, values at the points, Euler fluxes (and the
+//     driving source) to shared memory;
+//  B) one warp per conserved variable: the N accumulators of one (cell,
+//     variable) in registers, projection onto the basis gradients (and the
+//     source onto the basis), every table value a constant-bank operand.
+// After the last chunk, the six face fluxes are projected onto the face
+// traces; then R, or the FP64 SSP-RK3 stage combination and the limiter
+// screen (cells failing it are queued for the full limiter).
+template <int K, int MODE, bool FORCE>
+__global__ void __launch_bounds__(VolF32<K>::THREADS, VolF32<K>::MINB) volume_f32_kernel(
+    const double* __restrict__ yin, const float* __restrict__ fh, const float* __restrict__ field,
+    const double* __restrict__ tab64, Geo g, StageArgs st, double* __restrict__ R, Ctrl* ctrl) {
+  using TB = Tab<K>;
+  using CF = VolF32<K>;
+  constexpr int N = TB::N, Q2 = TB::Q2, C = CF::C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* sM = reinterpret_cast<double*>(smem_raw);  // [5][C] stage means
+  double* sA = sM + 5 * C;                            // [5][C] sum |w_l| max|phi_l|
+  float* sW = reinterpret_cast<float*>(sA + 5 * C);   // [5N][C]
+  float* sF = sW + 5 * N * C;                         // [15][PC][C]
+  float* sS = sF + 15 * CF::PC * C;                   // [4][PC][C]
+  const long long nc = g.nc;
+  const long long c0 = (long long)blockIdx.x * C;
+  const int tid = threadIdx.x;
+  const double* ysrc = (MODE == MODE_STAGE) ? st.ys : yin;
+  for (int it = tid; it < 5 * N * C; it += CF::THREADS) {
+    const int c = it % C, r = it / C;
+    const long long cell = c0 + c;
+    sW[r * C + c] = cell < nc ? (float)ysrc[(size_t)r * nc + cell] : (r == 0 ? 1.f : 0.f);
+  }
+  __syncthreads();
+  const float idx[3] = {(float)g.inv_dx[0], (float)g.inv_dx[1], (float)g.inv_dx[2]};
+  const float gm1 = (float)(g.gamma - 1.0);
+  float acc[N];
+#pragma unroll
+  for (int l = 0; l < N; ++l) acc[l] = 0.f;
+  vol_f32_chunk<K, 0, FORCE>(sW, sF, sS, field, c0, nc, gm1, idx, acc);
+  if (CF::NCH > 1) vol_f32_chunk<K, (CF::NCH > 1 ? 1 : 0), FORCE>(sW, sF, sS, field, c0, nc, gm1, idx, acc);
+  if (CF::NCH > 2) vol_f32_chunk<K, (CF::NCH > 2 ? 2 : 0), FORCE>(sW, sF, sS, field, c0, nc, gm1, idx, acc);
+  const int c = tid % C, i = tid / C;  // i: conserved variable, warp-uniform
+  const long long cell = c0 + c;
+  const bool live = cell < nc;
+  if (live) {
+    int ix, iy, iz;
+    cell_xyz(cell, g, ix, iy, iz);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const long long cu = neighbour(g, ix, iy, iz, d, +1);
+#pragma unroll
+      for (int p = 0; p < Q2; ++p) {
+        const size_t base = ((size_t)(d * 5 + i) * Q2 + p) * nc;
+        const float fm = __ldg(fh + base + cell) * idx[d];
+        const float fp = __ldg(fh + base + cu) * idx[d];
+#pragma unroll
+        for (int l = 0; l < N; ++l)
+          acc[l] += fm * c_tab32[TB::FPHIW + ((d * 2 + 0) * Q2 + p) * N + l] -
+                    fp * c_tab32[TB::FPHIW + ((d * 2 + 1) * Q2 + p) * N + l];
+      }
+    }
+  }
+  if (MODE == MODE_RHS) {
+    if (live) {
+#pragma unroll
+      for (int l = 0; l < N; ++l) R[(size_t)(i * N + l) * nc + cell] = -(double)acc[l];
+    }
+    return;
+  }
+  double sabs = 0.0, mean = 0.0;
+  bool finite = true;
+  if (live) {
+#pragma unroll
+    for (int l = 0; l < N; ++l) {
+      const size_t a = (size_t)(i * N + l) * nc + cell;
+      const double v = st.a0 * __ldcg(st.y0 + a) + st.b0 * (__ldcg(st.ys + a) + st.dt * (double)acc[l]);
+      st.out[a] = v;
+      finite &= isfinite(v);
+      if (l == 0) mean = v;
+      else sabs += fabs(v) * __ldg(tab64 + TB::LMAX + l);
+    }
+  }
+  sM[i * C + c] = finite ? mean : __longlong_as_double(0x7ff8000000000000LL);  // NaN marks non-finite
+  sA[i * C + c] = sabs;
+  __syncthreads();
+  if (tid < C && live) {
+    double m[5], a[5];
+    bool fin = true;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+      m[j] = sM[j * C + tid];
+      a[j] = sA[j * C + tid];
+      fin &= isfinite(m[j]);
+    }
+    if (!limiter_screen<K>(m, a, fin, g.gamma, g.eps_rho, g.eps_p)) {
+      const unsigned slot = atomicAdd(&ctrl->n_flag, 1u);
+      st.list[slot] = (int)cell;
+    }
+  }
+}
+
+// Full positivity limiter on the cells queued by a stage kernel (list of
+// *count cells).
+template <int K>
+__global__ void __launch_bounds__(kThreads) limit_list_kernel(double* __restrict__ y, const int* __restrict__ list,
+                                                              const unsigned* count, const double* __restrict__ tab64,
+                                                              Geo g, Ctrl* ctrl, int count_queued) {
+  const unsigned n = *count;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    atomicAdd(&ctrl->n_full_total, (unsigned long long)n);
+    if (count_queued) atomicAdd(&ctrl->n_queued_total, (unsigned long long)n);
+  }
+  unsigned e = 0;
+  for (unsigned i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads)
+    limit_cell<K>(y + list[i], g.nc, tab64, g.gamma, g.eps_rho, g.eps_p, &e);
+  if (e) atomicOr(&ctrl->err, e);
+}
+
+// screen[c] = 1 when cell c fails the limiter screen (capture of training data)
+template <int K>
+__global__ void __launch_bounds__(kThreads) screen_kernel(const double* __restrict__ y, uint8_t* __restrict__ screen,
+                                                          const double* __restrict__ tab64, Geo g) {
+  constexpr int N = nmodes(K);
+  const long long cell = (long long)blockIdx.x * kThreads + threadIdx.x;
+  if (cell >= g.nc) return;
+  double m[5], a[5];
+  bool fin = true;
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    m[i] = y[(size_t)(i * N) * g.nc + cell];
+    double sa = 0.0;
+    for (int l = 1; l < N; ++l) {
+      const double v = y[(size_t)(i * N + l) * g.nc + cell];
+      sa += fabs(v) * __ldg(tab64 + Tab<K>::LMAX + l);
+      fin &= isfinite(v);
+    }
+    fin &= isfinite(m[i]);
+    a[i] = sa;
+  }
+  screen[cell] = limiter_screen<K>(m, a, fin, g.gamma, g.eps_rho, g.eps_p) ? 0 : 1;
 }
 
 // ------------------------------------------------------ standalone limiter
@@ -309,30 +687,36 @@ __global__ void __launch_bounds__(kThreads) cfl_kernel(const double* __restrict_
 
 // ------------------------------------------------------- energy reset
 // Sect. 3.2: at every volume point rho eps = c^2/(gamma-1) rho (rho/rho0)^(gamma-1),
-// E_q = 1/2 |m_q|^2 / rho_q + rho_q eps_q, energy modes re-projected; then the
-// limiter. part[blockIdx.x] receives the block's sum of (e_before - e_after).
+// E_q = 1/2 |m_q|^2 / rho_q + rho_q eps_q, energy modes re-projected (one
+// thread per (cell, mode)); only the energy rows are written back. Cells
+// that then fail the limiter screen are queued (list / ctrl->n_flag) for the
+// full limiter. part[blockIdx.x] receives the block's sum of
+// (e_before - e_after), e = E - |m|^2 / (2 rho) from the means.
 template <int K, typename T, int C>
 __global__ void __launch_bounds__(kThreads) energy_reset_kernel(double* __restrict__ y, const T* __restrict__ tab,
                                                                 const double* __restrict__ tab64, Geo g, double c2g,
                                                                 double inv_rho0, double* __restrict__ part,
-                                                                Ctrl* ctrl) {
+                                                                int* __restrict__ list, Ctrl* ctrl) {
   using TB = Tab<K>;
   constexpr int N = TB::N, Q3 = TB::Q3;
   __shared__ T sW[4 * N * C];
   __shared__ T sE[Q3 * C];
-  __shared__ double sY[5 * N * C];
+  __shared__ double sEn[N * C];   // new energy modes
+  __shared__ double sM[5 * C];    // means (old energy mean in row 4)
   __shared__ double s_red[kThreads / 32];
-  __shared__ unsigned s_err;
   const long long nc = g.nc;
   const long long c0 = (long long)blockIdx.x * C;
   const int tid = threadIdx.x;
-  if (tid == 0) s_err = 0u;
-  for (int it = tid; it < 5 * N * C; it += kThreads) {
+  for (int it = tid; it < 4 * N * C; it += kThreads) {
     const int c = it % C, r = it / C;
     const long long cell = c0 + c;
     const double v = cell < nc ? y[(size_t)r * nc + cell] : (r == 0 ? 1.0 : 0.0);
-    sY[r * C + c] = v;
-    if (r < 4 * N) sW[r * C + c] = (T)v;
+    sW[r * C + c] = (T)v;
+    if (r % N == 0) sM[(r / N) * C + c] = v;
+  }
+  for (int c = tid; c < C; c += kThreads) {
+    const long long cell = c0 + c;
+    sM[4 * C + c] = cell < nc ? y[(size_t)(4 * N) * nc + cell] : 0.0;
   }
   __syncthreads();
   const T gm1 = (T)(g.gamma - 1.0);
@@ -352,28 +736,43 @@ __global__ void __launch_bounds__(kThreads) energy_reset_kernel(double* __restri
     sE[q * C + c] = T(0.5) * (U[1] * U[1] + U[2] * U[2] + U[3] * U[3]) / U[0] + U[0] * eps;
   }
   __syncthreads();
+  for (int it = tid; it < N * C; it += kThreads) {
+    const int c = it % C, l = it / C;
+    T acc = T(0);
+    for (int q = 0; q < Q3; ++q) acc += sE[q * C + c] * __ldg(tab + TB::VPHIW + q * N + l);
+    sEn[l * C + c] = (double)acc;
+  }
+  __syncthreads();
   double diss = 0.0;
   if (tid < C && c0 + tid < nc) {
     const int c = tid;
-    const double before = sY[(4 * N) * C + c] - 0.5 * (sY[N * C + c] * sY[N * C + c] + sY[2 * N * C + c] * sY[2 * N * C + c] +
-                                                      sY[3 * N * C + c] * sY[3 * N * C + c]) / sY[c];
-    T acc[N];
+    const long long cell = c0 + c;
+    const double r = sM[c], m1 = sM[C + c], m2 = sM[2 * C + c], m3 = sM[3 * C + c];
+    const double kin = 0.5 * (m1 * m1 + m2 * m2 + m3 * m3) / r;
+    diss = (sM[4 * C + c] - kin) - (sEn[c] - kin);
+    // limiter screen on the reset state (density and momentum unchanged)
+    double m[5] = {r, m1, m2, m3, sEn[c]}, a[5];
+    bool fin = true;
 #pragma unroll
-    for (int l = 0; l < N; ++l) acc[l] = T(0);
-    for (int q = 0; q < Q3; ++q) {
-      const T e = sE[q * C + c];
-      const T* pw = tab + TB::VPHIW + q * N;
-#pragma unroll
-      for (int l = 0; l < N; ++l) acc[l] += e * __ldg(pw + l);
+    for (int i = 0; i < 4; ++i) {
+      double sa = 0.0;
+      for (int l = 1; l < N; ++l) {
+        const double v = (double)sW[(i * N + l) * C + c];
+        sa += fabs(y[(size_t)(i * N + l) * nc + cell]) * __ldg(tab64 + TB::LMAX + l);
+        fin &= isfinite(v);
+      }
+      a[i] = sa;
     }
-#pragma unroll
-    for (int l = 0; l < N; ++l) sY[(4 * N + l) * C + c] = (double)acc[l];
-    const double after = sY[(4 * N) * C + c] - 0.5 * (sY[N * C + c] * sY[N * C + c] + sY[2 * N * C + c] * sY[2 * N * C + c] +
-                                                     sY[3 * N * C + c] * sY[3 * N * C + c]) / sY[c];
-    diss = before - after;
-    unsigned e = 0;
-    limit_cell<K>(sY + c, C, tab64, g.gamma, g.eps_rho, g.eps_p, &e);
-    if (e) atomicOr(&s_err, e);
+    double sa = 0.0;
+    for (int l = 1; l < N; ++l) {
+      sa += fabs(sEn[l * C + c]) * __ldg(tab64 + TB::LMAX + l);
+      fin &= isfinite(sEn[l * C + c]);
+    }
+    a[4] = sa;
+    if (!limiter_screen<K>(m, a, fin, g.gamma, g.eps_rho, g.eps_p)) {
+      const unsigned slot = atomicAdd(&ctrl->n_flag, 1u);
+      list[slot] = (int)cell;
+    }
   }
   // block sum of the dissipation (fixed order: deterministic)
 #pragma unroll
@@ -381,15 +780,14 @@ __global__ void __launch_bounds__(kThreads) energy_reset_kernel(double* __restri
   if ((tid & 31) == 0) s_red[tid >> 5] = diss;
   __syncthreads();
   if (tid == 0) {
-    double s = 0.0;
-    for (int w = 0; w < kThreads / 32; ++w) s += s_red[w];
-    part[blockIdx.x] = s;
-    if (s_err) atomicOr(&ctrl->err, s_err);
+    double sum = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) sum += s_red[w];
+    part[blockIdx.x] = sum;
   }
-  for (int it = tid; it < 5 * N * C; it += kThreads) {
-    const int c = it % C, r = it / C;
+  for (int it = tid; it < N * C; it += kThreads) {
+    const int c = it % C, l = it / C;
     const long long cell = c0 + c;
-    if (cell < nc) y[(size_t)r * nc + cell] = sY[r * C + c];
+    if (cell < nc) y[(size_t)(4 * N + l) * nc + cell] = sEn[l * C + c];
   }
 }
 

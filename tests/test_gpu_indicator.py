@@ -1,0 +1,180 @@
+"""Learned troubled-cell indicator on the GPU vs the FP64 numpy oracle
+(oracle/mlp.py): features, BF16 forward and backward through the C ABI.
+
+The GPU computes in BF16 with FP32 accumulation; the oracle comparison
+mirrors the BF16 roundings the kernels apply to their operands (X, W1, W2,
+the layer-1 activations), so the remaining differences come from FP32
+accumulation order and, in the backward pass, the BF16 rounding of the
+back-propagated pre-activation gradients:
+  features: within one BF16 ulp;  forward: 5e-3 of the logit scale;
+  backward: relative L2 error per tensor <= 2e-2 and cosine >= 0.999.
+"""
+import numpy as np
+import pytest
+
+import synthetic as syn
+from oracle import mlp
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dg():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_1602_09079_gb300 as m
+    m.load()
+    return m
+
+
+def bf16(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def flat(P):
+    return np.concatenate([P["W1"].ravel(), P["b1"], P["W2"].ravel(), P["b2"], P["w3"], P["b3"]]).astype(np.float32)
+
+
+def unflat(v, F):
+    H = mlp.HIDDEN
+    o = 0
+    out = {}
+    for key, shape in (("W1", (H, F)), ("b1", (H,)), ("W2", (H, H)), ("b2", (H,)), ("w3", (H,)), ("b3", (1,))):
+        size = int(np.prod(shape))
+        out[key] = np.asarray(v[o:o + size], dtype=np.float64).reshape(shape)
+        o += size
+    return out
+
+
+def mirrored(P):
+    """Parameters as the kernels see them (weights rounded to BF16)."""
+    Q = {k: np.asarray(v, dtype=np.float64) for k, v in P.items()}
+    Q["W1"] = bf16(Q["W1"])
+    Q["W2"] = bf16(Q["W2"])
+    for k in ("b1", "b2", "w3", "b3"):
+        Q[k] = np.asarray(Q[k], dtype=np.float32).astype(np.float64)
+    return Q
+
+
+def forward_mirrored(P, X):
+    z1 = X @ P["W1"].T + P["b1"]
+    h1 = bf16(np.maximum(z1, 0.0))
+    z2 = h1 @ P["W2"].T + P["b2"]
+    h2 = np.maximum(z2, 0.0)
+    return {"z1": z1, "h1": h1, "z2": z2, "h2": h2, "logit": h2 @ P["w3"] + P["b3"][0]}
+
+
+def rand_params(F, seed):
+    rng = np.random.default_rng(seed)
+    P = mlp.init_params(F, seed)
+    P["b1"] = 0.1 * rng.normal(size=P["b1"].shape)
+    P["b2"] = 0.1 * rng.normal(size=P["b2"].shape)
+    P["b3"] = np.array([0.2])
+    return {k: np.asarray(v, dtype=np.float32).astype(np.float64) for k, v in P.items()}
+
+
+@pytest.mark.parametrize("order", [2, 3, 4])
+def test_features_match_oracle(dg, order):
+    import torch
+    k, g = order - 1, syn.GAMMA
+    n = (7, 6, 5)
+    s = dg.Solver(n, order, g)
+    w = syn.random_state(n, s.N, g, seed=31 + order, high=0.05)
+    s.set_state(w)
+    nf, F, npar, _ = dg.dg_indicator_sizes(order)
+    assert nf == mlp.n_features(k) and F == mlp.n_features_padded(k)
+    X = torch.empty((s.ncells, F), dtype=torch.bfloat16, device="cuda")
+    dg.dg_indicator_features(s.ctx, None, X)
+    torch.cuda.synchronize()
+    got = X.to(torch.float64).cpu().numpy()
+    ref = bf16(mlp.features(w, k, g))
+    ulp = np.abs(ref) * 2.0 ** -7 + 1e-30
+    assert np.all(np.abs(got - ref) <= ulp), np.max(np.abs(got - ref) / ulp)
+
+
+@pytest.mark.parametrize("order", [2, 3, 4])
+def test_forward_matches_oracle(dg, order):
+    import torch
+    k = order - 1
+    nf, F, npar, _ = dg.dg_indicator_sizes(order)
+    rng = np.random.default_rng(40 + order)
+    n = 1000  # several 128-row tiles and a ragged tail
+    X = bf16(rng.normal(size=(n, F)))
+    P = rand_params(F, 41 + order)
+    Xd = torch.from_numpy(X).to(torch.bfloat16).cuda()
+    Pd = torch.from_numpy(flat(P)).cuda()
+    out = torch.full((n,), float("nan"), dtype=torch.float32, device="cuda")
+    dg.dg_indicator_forward(order, Xd, n, Pd, out, 0)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().astype(np.float64)
+    ref = forward_mirrored(mirrored(P), X)["logit"]
+    assert np.all(np.isfinite(got))
+    assert np.max(np.abs(got - ref)) <= 5e-3 * np.max(np.abs(ref)) + 1e-4
+
+
+@pytest.mark.parametrize("order", [2, 3, 4])
+def test_backward_matches_oracle(dg, order):
+    import torch
+    nf, F, npar, work = dg.dg_indicator_sizes(order)
+    rng = np.random.default_rng(50 + order)
+    n, a = 1000, 3.0
+    X = bf16(rng.normal(size=(n, F)))
+    y = (rng.uniform(size=n) < 0.3).astype(np.float64)
+    P = rand_params(F, 51 + order)
+    Q = mirrored(P)
+    cache = forward_mirrored(Q, X)
+    gref = mlp.backward(Q, X, cache, y, a)
+    lref = mlp.loss(cache["logit"], y, a)
+    Xd = torch.from_numpy(X).to(torch.bfloat16).cuda()
+    yd = torch.from_numpy(y.astype(np.float32)).cuda()
+    Pd = torch.from_numpy(flat(P)).cuda()
+    G = torch.zeros(npar + 1, dtype=torch.float32, device="cuda")
+    Wk = torch.empty(work, dtype=torch.uint8, device="cuda")
+    dg.dg_indicator_backward(order, Xd, yd, n, a, Pd, G, Wk, work, 0)
+    torch.cuda.synchronize()
+    gv = G.cpu().numpy().astype(np.float64)
+    got = unflat(gv[:npar], F)
+    assert abs(gv[npar] - lref) <= 1e-3 * abs(lref)
+    for key in gref:
+        r, q = gref[key].ravel(), got[key].ravel()
+        rel = np.linalg.norm(q - r) / max(np.linalg.norm(r), 1e-30)
+        cos = q @ r / max(np.linalg.norm(q) * np.linalg.norm(r), 1e-30)
+        assert rel <= 2e-2 and cos >= 0.999, (key, rel, cos)
+    # deterministic: a second call gives the same bits
+    G2 = torch.zeros_like(G)
+    dg.dg_indicator_backward(order, Xd, yd, n, a, Pd, G2, Wk, work, 0)
+    torch.cuda.synchronize()
+    assert torch.equal(G, G2)
+
+
+def test_training_on_gpu_reduces_loss(dg):
+    """A linearly separable labelling of random features is learned by the
+    GPU's own backward + Adam kernels."""
+    import torch
+    order = 3
+    nf, F, npar, work = dg.dg_indicator_sizes(order)
+    rng = np.random.default_rng(60)
+    n = 8192
+    X = bf16(rng.normal(size=(n, F)))
+    u = rng.normal(size=F)
+    y = (X @ u > 0.5).astype(np.float32)
+    Xd = torch.from_numpy(X).to(torch.bfloat16).cuda()
+    yd = torch.from_numpy(y).cuda()
+    Pd = torch.from_numpy(flat(rand_params(F, 61))).cuda()
+    m = torch.zeros_like(Pd)
+    v = torch.zeros_like(Pd)
+    G = torch.zeros(npar + 1, dtype=torch.float32, device="cuda")
+    Wk = torch.empty(work, dtype=torch.uint8, device="cuda")
+    losses = []
+    for step in range(1, 201):
+        dg.dg_indicator_backward(order, Xd, yd, n, 1.0, Pd, G, Wk, work, 0)
+        if step == 1 or step == 200:
+            losses.append(float(G[npar]))
+        dg.dg_indicator_adam(Pd, m, v, G, npar, 3e-3, 0.9, 0.999, 1e-8, step, 0)
+    torch.cuda.synchronize()
+    logits = torch.empty(n, dtype=torch.float32, device="cuda")
+    dg.dg_indicator_forward(order, Xd, n, Pd, logits, 0)
+    acc = float(((logits > 0).float() == yd).float().mean())
+    assert losses[1] < 0.3 * losses[0], losses
+    assert acc > 0.95, acc
