@@ -56,6 +56,10 @@ def parse():
     ap.add_argument("--err-steps", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--sweep", action="store_true",
+                    help="convergence sweep of the smooth diagonal density wave (16^3..64^3, orders 2..4, t = 1)")
+    ap.add_argument("--sweep-max-cells", type=int, default=64 ** 3 * 10 // 4,
+                    help="skip (n, order) pairs with n^3 N(k) above this many DOF per variable x 4")
     ap.add_argument("--precisions", default="fp64,mixed",
                     help="comma list of fp64,mixed (the first listed of mixed/fp64 is the headline)")
     return ap.parse_args()
@@ -197,6 +201,18 @@ def roofline_entry(kind, achieved, peak, unit, bound, traffic=None):
             "frac": (achieved / peak) if peak else None, "traffic": traffic}
 
 
+def ncu_traffic():
+    """DRAM bytes per cell per launch of the profiled kernels, from the ncu
+    capture summarised in profiles/ncu_traffic.json (a smaller mesh of the
+    same workload; traffic scales with the cells processed)."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(p) as f:
+            return json.load(f).get("kernels", {})
+    except (OSError, ValueError):
+        return {}
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -295,17 +311,20 @@ def run_ours(args):
         del y64, ymx, d
 
     # end-to-end through the public API with host buffers
-    s.set_precision(dgm.DG_PREC_MIXED)
-    host_in = torch.from_numpy(w0_dev.cpu().numpy()).pin_memory()
-    host_out = torch.empty_like(host_in).pin_memory()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        dgm.dg_set_state(s.ctx, host_in.data_ptr(), 0)
-        one_step()
-        dgm.dg_get_state(s.ctx, host_out.data_ptr(), 0)
-    torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
+    s.set_precision(dgm.DG_PREC_MIXED if "mixed" in results else dgm.DG_PREC_FP64)
+    e2e_s = 0.0
+    if args.e2e_steps > 0:
+        host_in = torch.from_numpy(w0_dev.cpu().numpy()).pin_memory()
+        host_out = torch.empty_like(host_in).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            dgm.dg_set_state(s.ctx, host_in.data_ptr(), 0)
+            one_step()
+            dgm.dg_get_state(s.ctx, host_out.data_ptr(), 0)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        del host_in, host_out
     e2e_s = max(max_over_ranks(world, e2e_s, dev), 1e-30)
     e2e_dof = sum_over_ranks(world, float(nc) * N * 3 * args.e2e_steps, dev)
     state_bytes = 5 * N * nc * 8
@@ -336,7 +355,13 @@ def run_ours(args):
         else:
             e = roofline_entry("hbm", byts / per_launch_s / 1e9, hbm, "GB/s", "hbm")
             e["peak_source"] = "measured (MEASURED_PEAKS.json hbm_gbs)"
-        e["kernel"] = f"volume_kernel<K={k}, {'double' if tsize == 8 else 'float'}, stage, forcing>"
+        kname = (f"volume_f32_kernel<{k}, 1, 1>" if (tsize == 4 and k <= 2)
+                 else f"volume_kernel<{k}, {'double' if tsize == 8 else 'float'}, 1, 1>")
+        e["kernel"] = kname + " (stage, forcing)"
+        tr = ncu_traffic().get(kname)
+        if tr:
+            e["traffic"] = tr["dram_bytes_per_cell"] * nc
+            e["traffic_source"] = tr.get("source")
         e["flops_per_launch"] = flops
         e["bytes_per_launch"] = byts
         e["ms_per_launch"] = per_launch_s * 1e3
@@ -456,8 +481,69 @@ def run_reference(args):
     }))
 
 
+def l2_density_error(w, k, n, exact, nq=6):
+    """L2 error of the density polynomial against exact(x, y, z) with an
+    nq-point Gauss rule per axis per cell (numpy Legendre basis)."""
+    import numpy.polynomial.legendre as npl
+    modes = [(u, v, d - u - v) for d in range(k + 1) for u in range(d, -1, -1) for v in range(d - u, -1, -1)]
+    xg, wg = npl.leggauss(nq)
+    P = np.array([[math.sqrt(2 * u + 1) * npl.legval(x, [0] * u + [1]) for x in xg] for u in range(k + 1)])
+    dx = 1.0 / n
+    X = (np.arange(n)[:, None] + 0.5 + 0.5 * xg[None, :]) * dx
+    W = (wg[:, None, None] * wg[None, :, None] * wg[None, None, :]) * (dx / 2) ** 3
+    err = 0.0
+    for iz in range(n):  # one z-slab at a time keeps memory small
+        rho = np.zeros((n, n, nq, nq, nq))
+        for l, (u, v, ww) in enumerate(modes):
+            rho += w[iz, :, :, 0, l][..., None, None, None] * (
+                P[u][None, None, None, None, :] * P[v][None, None, None, :, None] * P[ww][None, None, :, None, None])
+        ex = exact(X[None, :, None, None, :], X[:, None, None, :, None], X[iz][None, None, :, None, None])
+        err += np.sum((rho - ex) ** 2 * W[None, None])
+    return math.sqrt(err)
+
+
+def run_sweep(args):
+    """Plain FP64 convergence sweep: rho = 1 + 0.2 sin(2 pi (x+y+z)), v = (1,1,1),
+    p = 1, gamma = 5/3, SSP-RK3 at CFL 0.3 to t = 1, where the exact solution
+    equals the initial profile."""
+    import torch
+    import paper_1602_09079_gb300 as dgm
+    dgm.load()
+    fn = syn.smooth_wave_diag(GAMMA)
+    out = {"workload": "smooth diagonal density wave, FP64, t = 1", "runs": []}
+    for order in (2, 3, 4):
+        k = order - 1
+        N = order * (order + 1) * (order + 2) // 6
+        errs = []
+        for n in (16, 32, 64):
+            if n ** 3 * N > args.sweep_max_cells * 4:
+                out["runs"].append({"n": n, "order": order, "skipped": "above --sweep-max-cells"})
+                continue
+            s = dgm.Solver((n, n, n), order, GAMMA)
+            s.project_fn(fn)
+            t, steps, t0 = 0.0, 0, time.perf_counter()
+            while t < 1.0 - 1e-14:
+                dt = min(s.cfl_dt(args.courant), 1.0 - t)
+                s.step(dt)
+                t += dt
+                steps += 1
+            s.check()
+            wall = time.perf_counter() - t0
+            err = l2_density_error(s.get_state(), k, n, lambda x, y, z: 1 + 0.2 * np.sin(2 * np.pi * (x + y + z)))
+            errs.append((n, err))
+            rate = math.log2(errs[-2][1] / err) if len(errs) > 1 else None
+            out["runs"].append({"n": n, "order": order, "steps": steps, "l2_rho": err, "rate": rate,
+                                "wall_s": wall})
+            del s
+            torch.cuda.empty_cache()
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
+    if args.sweep:
+        run_sweep(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

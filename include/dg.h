@@ -103,11 +103,19 @@ int dg_get_state(dg_ctx* ctx, double* dst, int is_device);
  * (a along x). These are the points at which dg_project expects values. */
 int dg_quadrature_points(const dg_ctx* ctx, double* xyz_host);
 
+/* The same for the cells first .. first + count - 1 only (xyz_host holds
+ * count * Q^3 * 3 doubles), for meshes whose points do not fit at once. */
+int dg_quadrature_points_range(const dg_ctx* ctx, int64_t first, int64_t count, double* xyz_host);
+
 /* Initial L2 projection (Sect. 2.3, w_l = 1/8 sum_q q(x_q) phi_l(xi_q)
  * omega_q): q_points_dev holds conserved variables at the points of
  * dg_quadrature_points, device memory, layout [n_cells][5][Q^3]. Writes the
  * bound state (no limiting). */
 int dg_project(dg_ctx* ctx, const double* q_points_dev);
+
+/* dg_project for the cells first .. first + count - 1 (q_points_dev holds
+ * their count * 5 * Q^3 values); the other cells are left as they are. */
+int dg_project_range(dg_ctx* ctx, const double* q_points_dev, int64_t first, int64_t count);
 
 /* R(y) of Eq. dg:eqn:time: volume integral (Eq. dg:eqn:volume_int) plus
  * surface integral with the HLLC numerical flux (Eq. dg:eqn:surface_int),
@@ -185,9 +193,10 @@ int dg_kernel_stats(dg_ctx* ctx, int64_t* launches, double* ms);
  * No counterpart in the paper: a small network that predicts, per cell, the
  * flag of the positivity limiter's indicator (Sect. 2.5: the polynomial
  * leaves the positive set on S). Inputs per cell: the high modes scaled by the
- * cell means, log(rho), the mean Mach number, and the 26 neighbour means
- * relative to the cell's (include/dg.h order: own modes variable-major,
- * then the two scalars, then neighbours (dz,dy,dx) lexicographic in
+ * cell means, log(rho), the mean Mach number, the five excursion bounds
+ * sum_{l>=1} |w_il| max_S |phi_l| / s_i, and the 26 neighbour means relative
+ * to the cell's (in that order: own modes variable-major, the two scalars,
+ * the bounds, then neighbours (dz,dy,dx) lexicographic in
  * {-1,0,1}^3 without the centre, variable-minor), zero-padded to a multiple
  * of 32, in BF16. Network F -> 64 -> 64 -> 1 (ReLU, sigmoid); parameters FP32,
  * flat: W1[64][F], b1[64], W2[64][64], b2[64], w3[64], b3. Orders 2..4. */

@@ -11,6 +11,9 @@ cell:
         s_rho = |rho|, s_m = sqrt(|rho E|) for the three momenta, s_E = |E|
         from the cell means;
   extra log(rho_mean) and the mean Mach number |m|/rho / c;
+  bound sum_{l>=1} |w_{i,l}| max_S |phi_l| / s_i for i = 0..4, the largest
+        excursion of each variable's polynomial from its mean over the
+        positivity point set S (Sect. 2.5), relative to the scale s_i;
   nbr   (mean_i(neighbour) - mean_i(cell)) / s_i for the 26 neighbours of
         the 3x3x3 block, offsets (dz, dy, dx) in lexicographic order of
         {-1, 0, 1}^3 without (0,0,0), variable-minor;
@@ -26,7 +29,7 @@ HIDDEN = 64
 
 def n_features(k: int) -> int:
     N = (k + 1) * (k + 2) * (k + 3) // 6
-    return 5 * (N - 1) + 2 + 26 * 5
+    return 5 * (N - 1) + 2 + 5 + 26 * 5
 
 
 def n_features_padded(k: int) -> int:
@@ -37,6 +40,26 @@ def n_features_padded(k: int) -> int:
 def neighbour_offsets():
     return [(dz, dy, dx) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)
             if (dz, dy, dx) != (0, 0, 0)]
+
+
+def max_abs_basis_on_S(k):
+    """max over the positivity point set S of |phi_l|, from the oracle's own
+    Gauss/GLL rules and basis."""
+    import oracle
+    Q, m = k + 1, oracle.gll_count(k)
+    xg, _ = oracle.gauss(Q)
+    xh, _ = oracle.gll(m)
+    best = np.zeros(oracle.nmodes(k))
+    for al in range(3):
+        others = [o for o in range(3) if o != al]
+        for r in xh:
+            for a in xg:
+                for b in xg:
+                    xi = np.zeros(3)
+                    xi[al], xi[others[0]], xi[others[1]] = r, a, b
+                    phi, _ = oracle.basis(k, xi)
+                    best = np.maximum(best, np.abs(phi))
+    return best
 
 
 def features(w, k, gamma):
@@ -53,12 +76,14 @@ def features(w, k, gamma):
     c = np.sqrt(gamma * p / rho)
     mach = np.sqrt(m2) / rho / c
     extra = np.stack([np.log(rho), mach], axis=-1)
+    M = max_abs_basis_on_S(k)
+    bound = (np.abs(w[..., :, 1:]) @ M[1:]) / s
     nbr = []
     for dz, dy, dx in neighbour_offsets():
         shifted = np.roll(mean, shift=(-dz, -dy, -dx), axis=(0, 1, 2))
         nbr.append((shifted - mean) / s)
     nbr = np.concatenate(nbr, axis=-1)
-    X = np.concatenate([own, extra, nbr], axis=-1).reshape(-1, n_features(k))
+    X = np.concatenate([own, extra, bound, nbr], axis=-1).reshape(-1, n_features(k))
     out = np.zeros((X.shape[0], n_features_padded(k)))
     out[:, : X.shape[1]] = X
     return out

@@ -47,6 +47,8 @@ _SIGS = {
     "dg_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "dg_quadrature_points": (C.c_int, [C.c_void_p, C.c_void_p]),
     "dg_project": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "dg_project_range": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64]),
+    "dg_quadrature_points_range": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p]),
     "dg_rhs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "dg_step": (C.c_int, [C.c_void_p, C.c_double]),
     "dg_limit": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int64)]),
@@ -160,6 +162,15 @@ def dg_quadrature_points(ctx, xyz_host):
 
 def dg_project(ctx, q_points_dev):
     _check(load().dg_project(ctx, _ptr(q_points_dev)), "dg_project")
+
+
+def dg_project_range(ctx, q_points_dev, first, count):
+    _check(load().dg_project_range(ctx, _ptr(q_points_dev), int(first), int(count)), "dg_project_range")
+
+
+def dg_quadrature_points_range(ctx, first, count, xyz_host):
+    _check(load().dg_quadrature_points_range(ctx, int(first), int(count), _ptr(xyz_host)),
+           "dg_quadrature_points_range")
 
 
 def dg_rhs(ctx, y_dev, R_dev):
@@ -356,15 +367,20 @@ class Solver:
         dg_quadrature_points(self.ctx, xyz)
         return xyz
 
-    def project_fn(self, fn):
+    def project_fn(self, fn, chunk_cells=1 << 20):
         """Project a callable fn(x, y, z) -> (5, ...) at this library's own
-        quadrature points (device-side projection)."""
-        xyz = self.quadrature_points()
-        vals = np.asarray(fn(xyz[..., 0], xyz[..., 1], xyz[..., 2]), dtype=np.float64)
-        f = np.ascontiguousarray(np.moveaxis(vals, 0, 1))  # [nc][5][Q3]
-        fd = self.torch.from_numpy(f).to(self.device)
-        dg_project(self.ctx, fd)
-        self.stream.synchronize()
+        quadrature points (device-side projection), chunk_cells cells at a
+        time."""
+        Q3 = self.Q ** 3
+        for first in range(0, self.ncells, chunk_cells):
+            count = min(chunk_cells, self.ncells - first)
+            xyz = np.empty((count, Q3, 3))
+            dg_quadrature_points_range(self.ctx, first, count, xyz)
+            vals = np.asarray(fn(xyz[..., 0], xyz[..., 1], xyz[..., 2]), dtype=np.float64)
+            f = np.ascontiguousarray(np.moveaxis(vals, 0, 1))  # [count][5][Q3]
+            fd = self.torch.from_numpy(f).to(self.device)
+            dg_project_range(self.ctx, fd, first, count)
+            self.stream.synchronize()
 
     def rhs(self, canonical=True):
         R = self.torch.empty_like(self.y)

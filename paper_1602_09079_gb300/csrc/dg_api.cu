@@ -606,11 +606,16 @@ int dg_get_state(dg_ctx* c, double* dst, int is_device) {
 }
 
 int dg_quadrature_points(const dg_ctx* c, double* xyz) {
-  if (!c || !xyz) return DG_ERR_ARG;
+  if (!c) return DG_ERR_ARG;
+  return dg_quadrature_points_range(c, 0, c->geo.nc, xyz);
+}
+
+int dg_quadrature_points_range(const dg_ctx* c, int64_t first, int64_t count, double* xyz) {
+  if (!c || !xyz || first < 0 || count < 0 || first + count > c->geo.nc) return DG_ERR_ARG;
   const int Q = c->Q;
   double g[4], w[4];
   gauss_rule(Q, g, w);
-  for (long long cell = 0; cell < c->geo.nc; ++cell) {
+  for (long long cell = first; cell < first + count; ++cell) {
     const int ix = (int)(cell % c->geo.nx), iy = (int)((cell / c->geo.nx) % c->geo.ny),
               iz = (int)(cell / ((long long)c->geo.nx * c->geo.ny));
     const int ijk[3] = {ix, iy, iz};
@@ -620,7 +625,7 @@ int dg_quadrature_points(const dg_ctx* c, double* xyz) {
           const int q = a + Q * (b + Q * cc);
           const int ab[3] = {a, b, cc};
           for (int d = 0; d < 3; ++d)
-            xyz[((size_t)cell * Q * Q * Q + q) * 3 + d] =
+            xyz[((size_t)(cell - first) * Q * Q * Q + q) * 3 + d] =
                 (ijk[d] + 0.5) * c->geo.dx[d] + 0.5 * c->geo.dx[d] * g[ab[d]];
         }
   }
@@ -629,9 +634,15 @@ int dg_quadrature_points(const dg_ctx* c, double* xyz) {
 
 int dg_project(dg_ctx* c, const double* q_points_dev) {
   DG_TRY(need_bound(c));
-  if (!q_points_dev) return DG_ERR_ARG;
+  return dg_project_range(c, q_points_dev, 0, c->geo.nc);
+}
+
+int dg_project_range(dg_ctx* c, const double* q_points_dev, int64_t first, int64_t count) {
+  DG_TRY(need_bound(c));
+  if (!q_points_dev || first < 0 || count < 0 || first + count > c->geo.nc) return DG_ERR_ARG;
   DG_TRY(set_device(c));
-  DG_TRY(launch(c, KC_OTHER, [&] { return c->fn.project(q_points_dev, c->y, c->geo, c->stream); }));
+  if (count > 0)
+    DG_TRY(launch(c, KC_OTHER, [&] { return c->fn.project(q_points_dev, c->y, c->geo, first, count, c->stream); }));
   c->limited = false;
   return DG_OK;
 }
@@ -674,8 +685,8 @@ int dg_step(dg_ctx* c, double dt) {
     if (c->ind_params) {
       DG_CUDA(cudaMemsetAsync(&c->ctrl->n_gate, 0, sizeof(unsigned), c->stream));
       DG_TRY(launch(c, KC_LIMIT, [&] {
-        return dg::mlp::gate_for(c->k, out, c->geo, c->list, &c->ctrl->n_flag, c->ind_params, c->ind_logit_thr,
-                                 c->list2, &c->ctrl->n_gate, &c->ctrl->n_queued_total, c->stream);
+        return dg::mlp::gate_for(c->k, out, c->geo, c->fn.tab64(), c->list, &c->ctrl->n_flag, c->ind_params,
+                                 c->ind_logit_thr, c->list2, &c->ctrl->n_gate, &c->ctrl->n_queued_total, c->stream);
       }));
       DG_TRY(launch(c, KC_LIMIT, [&] {
         return c->fn.limit_list(out, c->list2, &c->ctrl->n_gate, c->geo, c->ctrl, 0, c->stream);
@@ -852,7 +863,9 @@ int dg_indicator_capture(dg_ctx* c, double dt, uint16_t* X_dev, int8_t* flags_de
     euler_stage_kernel<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(c->y, c->ybuf, dt, c->ybuf, n);
     return cudaGetLastError();
   }));
-  DG_TRY(launch(c, KC_OTHER, [&] { return dg::mlp::features_for(c->k, c->ybuf, c->geo, X_dev, c->stream); }));
+  DG_TRY(launch(c, KC_OTHER, [&] {
+    return dg::mlp::features_for(c->k, c->ybuf, c->geo, c->fn.tab64(), X_dev, c->stream);
+  }));
   DG_TRY(launch(c, KC_OTHER, [&] { return c->fn.screen(c->ybuf, screen_dev, c->geo, c->stream); }));
   DG_TRY(launch(c, KC_LIMIT, [&] { return c->fn.limit(c->ybuf, flags_dev, c->geo, c->ctrl, c->stream); }));
   return sync_and_check(c, nullptr);
@@ -875,7 +888,7 @@ int dg_indicator_features(dg_ctx* c, const double* y_dev, uint16_t* X_dev) {
   if (!X_dev || c->k < 1) return DG_ERR_ARG;
   DG_TRY(set_device(c));
   const double* y = y_dev ? y_dev : c->y;
-  return launch(c, KC_OTHER, [&] { return dg::mlp::features_for(c->k, y, c->geo, X_dev, c->stream); });
+  return launch(c, KC_OTHER, [&] { return dg::mlp::features_for(c->k, y, c->geo, c->fn.tab64(), X_dev, c->stream); });
 }
 
 int dg_set_timing(dg_ctx* c, int on) {

@@ -190,8 +190,8 @@ cudaError_t energy_reset(int prec, double* y, const Geo& g, double c2g, double i
               : reset_t<double>(y, g, c2g, inv_rho0, part, n_part, list, ctrl, s);
 }
 
-cudaError_t project(const double* f, double* y, const Geo& g, cudaStream_t s) {
-  project_kernel<KK><<<grid1(5 * g.nc, kThreads), kThreads, 0, s>>>(f, y, tab_ptr<double>(), g);
+cudaError_t project(const double* f, double* y, const Geo& g, long long first, long long count, cudaStream_t s) {
+  project_kernel<KK><<<grid1(5 * count, kThreads), kThreads, 0, s>>>(f, y, tab_ptr<double>(), g, first, count);
   return cudaGetLastError();
 }
 
@@ -226,6 +226,7 @@ Launchers DG_PASTE(launchers_k, DG_K)() {
   L.energy_reset = energy_reset;
   L.project = project;
   L.forcing_field = forcing_field;
+  L.tab64 = tab_ptr<double>;
   L.table_size = TB::SIZE;
   return L;
 }

@@ -794,21 +794,24 @@ __global__ void __launch_bounds__(kThreads) energy_reset_kernel(double* __restri
 // ------------------------------------------------------------- projection
 // w_l = 1/8 sum_q f(x_q) phi_l(xi_q) omega_q (Sect. 2.3), f canonical
 // [nc][5][Q^3]. One thread per (cell, variable).
+// Cells first .. first + count - 1; f holds their point values only.
 template <int K>
 __global__ void __launch_bounds__(kThreads) project_kernel(const double* __restrict__ f, double* __restrict__ y,
-                                                           const double* __restrict__ tab64, Geo g) {
+                                                           const double* __restrict__ tab64, Geo g, long long first,
+                                                           long long count) {
   using TB = Tab<K>;
   constexpr int N = TB::N, Q3 = TB::Q3;
   const long long nc = g.nc;
   const long long it = (long long)blockIdx.x * kThreads + threadIdx.x;
-  if (it >= 5 * nc) return;
-  const long long cell = it % nc;
-  const int i = (int)(it / nc);
+  if (it >= 5 * count) return;
+  const long long local = it % count;
+  const long long cell = first + local;
+  const int i = (int)(it / count);
   double acc[N];
 #pragma unroll
   for (int l = 0; l < N; ++l) acc[l] = 0.0;
   for (int q = 0; q < Q3; ++q) {
-    const double v = f[((size_t)cell * 5 + i) * Q3 + q];
+    const double v = f[((size_t)local * 5 + i) * Q3 + q];
     const double* pw = tab64 + TB::VPHIW + q * N;
 #pragma unroll
     for (int l = 0; l < N; ++l) acc[l] += v * __ldg(pw + l);

@@ -36,9 +36,12 @@ struct Launchers {
   // limiter screen afterwards are queued in list / ctrl->n_flag (0 on entry)
   cudaError_t (*energy_reset)(int prec, double* y, const Geo& g, double c2g, double inv_rho0, double* part,
                               int* n_part, int* list, Ctrl* ctrl, cudaStream_t s);
-  cudaError_t (*project)(const double* f, double* y, const Geo& g, cudaStream_t s);
+  // projection of the cells first .. first + count - 1
+  cudaError_t (*project)(const double* f, double* y, const Geo& g, long long first, long long count, cudaStream_t s);
   cudaError_t (*forcing_field)(int prec, void* field, const double* modes, int n_modes, const Geo& g,
                                const double* L, cudaStream_t s);
+  // the degree's FP64 table on the current device
+  const double* (*tab64)();
   size_t table_size;
 };
 

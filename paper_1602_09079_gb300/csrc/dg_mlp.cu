@@ -5,7 +5,8 @@
 //
 // Features per cell (FP64, rounded to BF16): own high modes w_{i,l}/s_i
 // (l >= 1, variable-major) with s = (|rho|, sqrt|rho E| x3, |E|) from the cell
-// means; log(rho) and the mean Mach number; the 26 neighbour means relative
+// means; log(rho) and the mean Mach number; the excursion bounds
+// sum_{l>=1} |w_{i,l}| max_S |phi_l| / s_i (i = 0..4); the 26 neighbour means relative
 // to the cell's, (mean_nb - mean)/s, offsets (dz,dy,dx) lexicographic in
 // {-1,0,1}^3 without the centre, variable-minor; zero padding to a multiple
 // of 32. Network: F -> 64 -> 64 -> 1 with ReLU, sigmoid output.
@@ -26,7 +27,7 @@ namespace {
 constexpr int H = 64;
 constexpr int kRows = 128;  // cells per tile (8 warps x 16 rows)
 
-__host__ __device__ constexpr int nfeat(int k) { return 5 * (nmodes(k) - 1) + 2 + 130; }
+__host__ __device__ constexpr int nfeat(int k) { return 5 * (nmodes(k) - 1) + 2 + 5 + 130; }
 __host__ __device__ constexpr int nfeat_pad(int k) { return (nfeat(k) + 31) / 32 * 32; }
 
 template <int F>
@@ -89,7 +90,8 @@ __device__ __forceinline__ void frag_bk(uint32_t (&b)[2], const bf16* S, int ld,
 
 // ------------------------------------------------------------- features
 template <int K>
-__device__ void cell_features(const double* __restrict__ y, const Geo& g, long long cell, double gamma, bf16* out) {
+__device__ void cell_features(const double* __restrict__ y, const Geo& g, long long cell, double gamma,
+                              const double* __restrict__ tab64, bf16* out) {
   constexpr int N = nmodes(K), F = nfeat_pad(K);
   const long long nc = g.nc;
   double mean[5];
@@ -105,6 +107,11 @@ __device__ void cell_features(const double* __restrict__ y, const Geo& g, long l
   const double c = sqrt(gamma * p / mean[0]);
   out[f++] = __double2bfloat16(log(mean[0]));
   out[f++] = __double2bfloat16(sqrt(m2) / mean[0] / c);
+  for (int i = 0; i < 5; ++i) {
+    double b = 0.0;
+    for (int l = 1; l < N; ++l) b += fabs(y[(size_t)(i * N + l) * nc + cell]) * __ldg(tab64 + Tab<K>::LMAX + l);
+    out[f++] = __double2bfloat16(b * inv_s[i]);
+  }
   const int cc = (int)cell;
   const int ix = cc % g.nx, iy = (cc / g.nx) % g.ny, iz = cc / (g.nx * g.ny);
   for (int dz = -1; dz <= 1; ++dz)
@@ -120,11 +127,12 @@ __device__ void cell_features(const double* __restrict__ y, const Geo& g, long l
 }
 
 template <int K>
-__global__ void __launch_bounds__(128) features_kernel(const double* __restrict__ y, Geo g, bf16* __restrict__ X) {
+__global__ void __launch_bounds__(128) features_kernel(const double* __restrict__ y, Geo g,
+                                                       const double* __restrict__ tab64, bf16* __restrict__ X) {
   constexpr int F = nfeat_pad(K);
   const long long cell = (long long)blockIdx.x * 128 + threadIdx.x;
   if (cell >= g.nc) return;
-  cell_features<K>(y, g, cell, g.gamma, X + (size_t)cell * F);
+  cell_features<K>(y, g, cell, g.gamma, tab64, X + (size_t)cell * F);
 }
 
 // ------------------------------------------------------ weights -> smem
@@ -496,6 +504,7 @@ __global__ void __launch_bounds__(256) backward_kernel(const bf16* __restrict__ 
 // whose logit reaches the threshold go on to list_out / *count_out.
 template <int K>
 __global__ void __launch_bounds__(256) gate_kernel(const double* __restrict__ y, Geo g,
+                                                   const double* __restrict__ tab64,
                                                    const int* __restrict__ list_in, const unsigned* count_in,
                                                    const float* __restrict__ P, float logit_thr,
                                                    int* __restrict__ list_out, unsigned* count_out,
@@ -521,7 +530,7 @@ __global__ void __launch_bounds__(256) gate_kernel(const double* __restrict__ y,
     if (threadIdx.x < kRows) {
       const unsigned r = tile * kRows + threadIdx.x;
       bf16* row = sX + threadIdx.x * L::LDX;
-      if (r < n) cell_features<K>(y, g, list_in[r], g.gamma, row);
+      if (r < n) cell_features<K>(y, g, list_in[r], g.gamma, tab64, row);
       else
         for (int f = 0; f < F; ++f) row[f] = __float2bfloat16(0.f);
     }
@@ -563,8 +572,8 @@ __global__ void adam_kernel(float* __restrict__ p, float* __restrict__ m, float*
 template <int K>
 struct Ops {
   static constexpr int F = nfeat_pad(K);
-  static cudaError_t features(const double* y, const Geo& g, void* X, cudaStream_t s) {
-    features_kernel<K><<<(unsigned)((g.nc + 127) / 128), 128, 0, s>>>(y, g, static_cast<bf16*>(X));
+  static cudaError_t features(const double* y, const Geo& g, const double* tab64, void* X, cudaStream_t s) {
+    features_kernel<K><<<(unsigned)((g.nc + 127) / 128), 128, 0, s>>>(y, g, tab64, static_cast<bf16*>(X));
     return cudaGetLastError();
   }
   static cudaError_t forward(const void* X, long long n, const float* P, float* logits, cudaStream_t s) {
@@ -576,12 +585,14 @@ struct Ops {
     forward_kernel<F><<<grid, 256, FwdSmem<F>::bytes(), s>>>(static_cast<const bf16*>(X), n, P, logits);
     return cudaGetLastError();
   }
-  static cudaError_t gate(const double* y, const Geo& g, const int* list_in, const unsigned* count_in, const float* P,
-                          float thr, int* list_out, unsigned* count_out, unsigned long long* queued, cudaStream_t s) {
+  static cudaError_t gate(const double* y, const Geo& g, const double* tab64, const int* list_in,
+                          const unsigned* count_in, const float* P, float thr, int* list_out, unsigned* count_out,
+                          unsigned long long* queued, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(gate_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)FwdSmem<F>::bytes());
     if (e != cudaSuccess) return e;
-    gate_kernel<K><<<152, 256, FwdSmem<F>::bytes(), s>>>(y, g, list_in, count_in, P, thr, list_out, count_out, queued);
+    gate_kernel<K><<<152, 256, FwdSmem<F>::bytes(), s>>>(y, g, tab64, list_in, count_in, P, thr, list_out, count_out,
+                                                         queued);
     return cudaGetLastError();
   }
   static cudaError_t backward(const void* X, const float* y, long long n, float pw, const float* P, float* grads,
@@ -678,21 +689,21 @@ int dg_indicator_adam(float* params, float* m, float* v, const float* grads, int
 
 namespace dg {
 namespace mlp {
-cudaError_t gate_for(int k, const double* y, const Geo& g, const int* list_in, const unsigned* count_in,
-                     const float* P, float logit_thr, int* list_out, unsigned* count_out,
+cudaError_t gate_for(int k, const double* y, const Geo& g, const double* tab64, const int* list_in,
+                     const unsigned* count_in, const float* P, float logit_thr, int* list_out, unsigned* count_out,
                      unsigned long long* queued_total, cudaStream_t s) {
   switch (k) {
-    case 1: return Ops<1>::gate(y, g, list_in, count_in, P, logit_thr, list_out, count_out, queued_total, s);
-    case 2: return Ops<2>::gate(y, g, list_in, count_in, P, logit_thr, list_out, count_out, queued_total, s);
-    default: return Ops<3>::gate(y, g, list_in, count_in, P, logit_thr, list_out, count_out, queued_total, s);
+    case 1: return Ops<1>::gate(y, g, tab64, list_in, count_in, P, logit_thr, list_out, count_out, queued_total, s);
+    case 2: return Ops<2>::gate(y, g, tab64, list_in, count_in, P, logit_thr, list_out, count_out, queued_total, s);
+    default: return Ops<3>::gate(y, g, tab64, list_in, count_in, P, logit_thr, list_out, count_out, queued_total, s);
   }
 }
 
-cudaError_t features_for(int k, const double* y, const Geo& g, void* X, cudaStream_t s) {
+cudaError_t features_for(int k, const double* y, const Geo& g, const double* tab64, void* X, cudaStream_t s) {
   switch (k) {
-    case 1: return Ops<1>::features(y, g, X, s);
-    case 2: return Ops<2>::features(y, g, X, s);
-    default: return Ops<3>::features(y, g, X, s);
+    case 1: return Ops<1>::features(y, g, tab64, X, s);
+    case 2: return Ops<2>::features(y, g, tab64, X, s);
+    default: return Ops<3>::features(y, g, tab64, X, s);
   }
 }
 }  // namespace mlp

@@ -70,7 +70,7 @@ def test_features_neighbour_offsets_and_scales():
     w[1, 2, 3, 0, 0] = 1.5
     w[1, 2, 2, 4, 2] = 0.6  # a high mode (l = 2) of the energy of cell (1,2,2)
     X = mlp.features(w, 1, g)
-    own, extra = 5 * 3, 2
+    own, extra = 5 * 3, 2 + 5  # log rho, Mach, then the five excursion bounds
     offs = mlp.neighbour_offsets()
     cell = (1 * 4 + 2) * 4 + 2  # (iz, iy, ix) = (1, 2, 2): its +x neighbour is the changed cell
     j = offs.index((0, 0, 1))
@@ -78,6 +78,10 @@ def test_features_neighbour_offsets_and_scales():
     assert abs(X[cell, own + extra + 5 * j + 4]) < 1e-15
     # energy high mode l=2 of cell (1,2,2) scaled by |E|
     assert abs(X[cell, 4 * 3 + 1] - 0.6 / 2.0) < 1e-15
+    # its excursion bound: mode 2 is sqrt(3) xi_y, whose largest |value| on S
+    # is sqrt(3) (the GLL end points of S_y)
+    assert abs(X[cell, own + 2 + 4] - 0.6 * math.sqrt(3) / 2.0) < 1e-15
+    assert np.all(X[cell, own + 2: own + 6] == 0)
     # the changed cell sees every neighbour at -0.5 / 1.5 in density
     cc = (1 * 4 + 2) * 4 + 3
     for j in range(26):
