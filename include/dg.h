@@ -256,8 +256,9 @@ int dg_indicator_adam(float* params, float* m, float* v, const float* grads, int
  * scratch, the face fluxes go to one fixed array in device memory,
  * DG_NOALLOC_SCRATCH_BYTES = 32 MiB, that every GPU which loads the library
  * holds until the process exits. Needs 15 (k+1)^2 n_cells x 8 bytes (FP64)
- * or x 4 bytes (DG_PREC_MIXED), plus 256: e.g. at most 31,000 cells at
- * order 3 in FP64; larger problems return DG_ERR_TOO_LARGE.
+ * or (15 (k+1)^2 + 5 N) n_cells x 4 bytes (DG_PREC_MIXED), plus 512: e.g. at
+ * most 31,000 cells at order 3 in FP64; larger problems return
+ * DG_ERR_TOO_LARGE.
  * mesh/order/gamma as in dg_init; precision DG_PREC_FP64 or DG_PREC_MIXED;
  * y_dev (input) and R_dev (output): device, state layout, 5 N n_cells doubles;
  * cuda_stream: cudaStream_t (NULL = legacy default stream), enqueued without

@@ -242,6 +242,12 @@ __global__ void state_to_canon_kernel(const double* __restrict__ in, double* __r
   }
 }
 
+// FP32 shadow of an FP64 state: yf = float(y)
+__global__ void to_f32_kernel(const double* __restrict__ y, float* __restrict__ yf, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) yf[i] = (float)y[i];
+}
+
 // out = y - dt * r (one forward-Euler stage, capture of training data)
 __global__ void euler_stage_kernel(const double* __restrict__ y, const double* __restrict__ r, double dt,
                                    double* __restrict__ out, long long n) {
@@ -315,6 +321,8 @@ struct dg_ctx {
   double* ybuf = nullptr;
   int* list = nullptr;
   int* list2 = nullptr;
+  float* yf = nullptr;        // FP32 shadow of the state (FP32 path, degrees <= 2)
+  bool shadow_valid = false;  // yf == float(y)
   // learned indicator gate (caller-owned FP32 parameters)
   const float* ind_params = nullptr;
   float ind_logit_thr = 0.f;
@@ -339,7 +347,7 @@ struct dg_ctx {
 namespace {
 
 struct Layout {
-  size_t ctrl, part, modes, sums, ybuf, list, list2, fh, field, base_end, full_end;
+  size_t ctrl, part, modes, sums, ybuf, list, list2, yf, fh, field, base_end, full_end;
 };
 
 Layout layout_of(const dg_ctx* c) {
@@ -361,6 +369,8 @@ Layout layout_of(const dg_ctx* c) {
   o += align256(sizeof(int) * nc);
   L.list2 = o;
   o += align256(sizeof(int) * nc);
+  L.yf = o;
+  o += align256(sizeof(float) * 5 * c->N * nc);
   L.fh = o;
   o += align256(sizeof(double) * 15 * c->Q * c->Q * nc);
   L.base_end = o;
@@ -438,6 +448,18 @@ int launch(dg_ctx* c, int cls, F&& f) {
 }
 
 enum { KC_LIMIT = 0, KC_FACE = 1, KC_VOLUME = 2, KC_CFL = 3, KC_RESET = 4, KC_OTHER = 5 };
+
+// true when the current precision's kernels read the FP32 shadow
+bool uses_shadow(const dg_ctx* c) { return c->prec == DG_PREC_MIXED && c->fn.f32_shadow; }
+
+// yf = float(y) (y: the bound state or any state-layout buffer)
+int convert_shadow(dg_ctx* c, const double* y) {
+  const long long n = (long long)5 * c->N * c->geo.nc;
+  return launch(c, KC_OTHER, [&] {
+    to_f32_kernel<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(y, c->yf, n);
+    return cudaGetLastError();
+  });
+}
 
 int refresh_field(dg_ctx* c) {
   if (c->n_force == 0) return DG_OK;
@@ -558,6 +580,8 @@ int dg_bind(dg_ctx* c, double* y_dev, void* scratch_dev, size_t scratch_bytes, v
   c->ybuf = reinterpret_cast<double*>(c->scratch + L.ybuf);
   c->list = reinterpret_cast<int*>(c->scratch + L.list);
   c->list2 = reinterpret_cast<int*>(c->scratch + L.list2);
+  c->yf = reinterpret_cast<float*>(c->scratch + L.yf);
+  c->shadow_valid = false;
   c->ind_params = nullptr;
   c->fh = c->scratch + L.fh;
   c->field = c->forcing_capable ? c->scratch + L.field : nullptr;
@@ -584,6 +608,7 @@ int dg_set_state(dg_ctx* c, const double* src, int is_device) {
     return cudaGetLastError();
   }));
   c->limited = false;
+  c->shadow_valid = false;
   return DG_OK;
 }
 
@@ -644,6 +669,7 @@ int dg_project_range(dg_ctx* c, const double* q_points_dev, int64_t first, int64
   if (count > 0)
     DG_TRY(launch(c, KC_OTHER, [&] { return c->fn.project(q_points_dev, c->y, c->geo, first, count, c->stream); }));
   c->limited = false;
+  c->shadow_valid = false;
   return DG_OK;
 }
 
@@ -653,9 +679,13 @@ int dg_rhs(dg_ctx* c, const double* y_dev, double* R_dev) {
   DG_TRY(set_device(c));
   const double* y = y_dev ? y_dev : c->y;
   const bool force = c->n_force > 0;
-  DG_TRY(launch(c, KC_FACE, [&] { return c->fn.face(c->prec, y, c->fh, c->geo, c->stream); }));
+  if (uses_shadow(c) && !(y == c->y && c->shadow_valid)) {
+    DG_TRY(convert_shadow(c, y));
+    c->shadow_valid = y == c->y;
+  }
+  DG_TRY(launch(c, KC_FACE, [&] { return c->fn.face(c->prec, y, c->yf, c->fh, c->geo, c->stream); }));
   DG_TRY(launch(c, KC_VOLUME, [&] {
-    return c->fn.volume_rhs(c->prec, force, y, c->fh, c->field, c->geo, R_dev, c->ctrl, c->stream);
+    return c->fn.volume_rhs(c->prec, force, y, c->yf, c->fh, c->field, c->geo, R_dev, c->ctrl, c->stream);
   }));
   return DG_OK;
 }
@@ -665,8 +695,13 @@ int dg_step(dg_ctx* c, double dt) {
   if (!(dt > 0.0) || !std::isfinite(dt)) return DG_ERR_ARG;
   DG_TRY(set_device(c));
   const bool force = c->n_force > 0;
-  if (!c->limited)
+  if (!c->limited) {
     DG_TRY(launch(c, KC_LIMIT, [&] { return c->fn.limit(c->y, nullptr, c->geo, c->ctrl, c->stream); }));
+    c->shadow_valid = false;
+  }
+  const bool shadow = uses_shadow(c);
+  if (shadow && !c->shadow_valid) DG_TRY(convert_shadow(c, c->y));
+  float* yf = shadow ? c->yf : nullptr;
   // Shu-Osher SSP-RK3: y1 = y0 - dt R(y0); y2 = 3/4 y0 + 1/4 (y1 - dt R(y1));
   // y3 = 1/3 y0 + 2/3 (y2 - dt R(y2)); each output limited for the next stage.
   const double a0[3] = {0.0, 0.75, 1.0 / 3.0};
@@ -674,11 +709,11 @@ int dg_step(dg_ctx* c, double dt) {
   const double* ys = c->y;
   for (int s = 0; s < 3; ++s) {
     double* out = s < 2 ? c->ybuf : c->y;
-    DG_TRY(launch(c, KC_FACE, [&] { return c->fn.face(c->prec, ys, c->fh, c->geo, c->stream); }));
+    DG_TRY(launch(c, KC_FACE, [&] { return c->fn.face(c->prec, ys, yf, c->fh, c->geo, c->stream); }));
     DG_CUDA(cudaMemsetAsync(&c->ctrl->n_flag, 0, sizeof(unsigned), c->stream));
     DG_TRY(launch(c, KC_VOLUME, [&] {
       return c->fn.volume_stage(c->prec, force, c->fh, c->field, c->geo, ys, c->y, out, a0[s], b0[s], dt, c->list,
-                                c->ctrl, c->stream);
+                                yf, c->ctrl, c->stream);
     }));
     // the limiter of the next stage's input: cells that failed the screen,
     // filtered by the learned indicator when one is set
@@ -689,16 +724,17 @@ int dg_step(dg_ctx* c, double dt) {
                                  c->ind_logit_thr, c->list2, &c->ctrl->n_gate, &c->ctrl->n_queued_total, c->stream);
       }));
       DG_TRY(launch(c, KC_LIMIT, [&] {
-        return c->fn.limit_list(out, c->list2, &c->ctrl->n_gate, c->geo, c->ctrl, 0, c->stream);
+        return c->fn.limit_list(out, c->list2, &c->ctrl->n_gate, c->geo, c->ctrl, 0, yf, c->stream);
       }));
     } else {
       DG_TRY(launch(c, KC_LIMIT, [&] {
-        return c->fn.limit_list(out, c->list, &c->ctrl->n_flag, c->geo, c->ctrl, 1, c->stream);
+        return c->fn.limit_list(out, c->list, &c->ctrl->n_flag, c->geo, c->ctrl, 1, yf, c->stream);
       }));
     }
     ys = out;
   }
   c->limited = true;
+  c->shadow_valid = shadow;
   return DG_OK;
 }
 
@@ -708,6 +744,7 @@ int dg_limit(dg_ctx* c, int8_t* flags_dev, int64_t* n_limited) {
   if (n_limited) DG_CUDA(cudaMemsetAsync(&c->ctrl->n_limited, 0, sizeof(unsigned long long), c->stream));
   DG_TRY(launch(c, KC_LIMIT, [&] { return c->fn.limit(c->y, flags_dev, c->geo, c->ctrl, c->stream); }));
   c->limited = true;
+  c->shadow_valid = false;
   if (n_limited) {
     Ctrl h{};
     int st = sync_and_check(c, &h);
@@ -786,15 +823,18 @@ int dg_energy_reset(dg_ctx* c, double c_iso, double rho0, double* dissipated) {
   DG_TRY(set_device(c));
   int n_part = 0;
   const double c2g = c_iso * c_iso / (c->geo.gamma - 1.0);
+  // keep the FP32 shadow current if it is (energy rows and limited cells)
+  float* yf = (uses_shadow(c) && c->shadow_valid) ? c->yf : nullptr;
+  if (!yf) c->shadow_valid = false;
   DG_CUDA(cudaMemsetAsync(&c->ctrl->n_flag, 0, sizeof(unsigned), c->stream));
   DG_TRY(launch(c, KC_RESET, [&] {
-    return c->fn.energy_reset(c->prec, c->y, c->geo, c2g, 1.0 / rho0, c->part, &n_part, c->list, c->ctrl,
+    return c->fn.energy_reset(c->prec, c->y, c->geo, c2g, 1.0 / rho0, c->part, &n_part, c->list, c->ctrl, yf,
                               c->stream);
   }));
   // the positivity limiter after the reset (Sect. 3.2): full limiter on the
   // cells that failed the screen
   DG_TRY(launch(c, KC_RESET, [&] {
-    return c->fn.limit_list(c->y, c->list, &c->ctrl->n_flag, c->geo, c->ctrl, 0, c->stream);
+    return c->fn.limit_list(c->y, c->list, &c->ctrl->n_flag, c->geo, c->ctrl, 0, yf, c->stream);
   }));
   c->limited = true;
   if (dissipated) {
@@ -855,9 +895,13 @@ int dg_indicator_capture(dg_ctx* c, double dt, uint16_t* X_dev, int8_t* flags_de
   DG_TRY(set_device(c));
   const bool force = c->n_force > 0;
   const long long n = (long long)5 * c->N * c->geo.nc;
-  DG_TRY(launch(c, KC_FACE, [&] { return c->fn.face(c->prec, c->y, c->fh, c->geo, c->stream); }));
+  if (uses_shadow(c) && !c->shadow_valid) {
+    DG_TRY(convert_shadow(c, c->y));
+    c->shadow_valid = true;
+  }
+  DG_TRY(launch(c, KC_FACE, [&] { return c->fn.face(c->prec, c->y, c->yf, c->fh, c->geo, c->stream); }));
   DG_TRY(launch(c, KC_VOLUME, [&] {
-    return c->fn.volume_rhs(c->prec, force, c->y, c->fh, c->field, c->geo, c->ybuf, c->ctrl, c->stream);
+    return c->fn.volume_rhs(c->prec, force, c->y, c->yf, c->fh, c->field, c->geo, c->ybuf, c->ctrl, c->stream);
   }));
   DG_TRY(launch(c, KC_OTHER, [&] {
     euler_stage_kernel<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(c->y, c->ybuf, dt, c->ybuf, n);
@@ -1013,8 +1057,11 @@ extern "C" int dg_rhs_noalloc(const dg_mesh* mesh, int order, double gamma, int 
   const int k = order - 1, Q = k + 1;
   const size_t tsize = precision == DG_PREC_MIXED ? sizeof(float) : sizeof(double);
   const size_t ctrl_bytes = 256;
-  if (nc > (long long)(kNoAllocBytes / tsize) ||
-      ctrl_bytes + (size_t)15 * Q * Q * (size_t)nc * tsize > kNoAllocBytes)
+  const Launchers L = launchers_for(k);
+  // FP32 path of degrees <= 2: an FP32 copy of y sits behind the face fluxes
+  const bool shadow = precision == DG_PREC_MIXED && L.f32_shadow;
+  const size_t per_cell = (size_t)15 * Q * Q * tsize + (shadow ? (size_t)5 * nmodes(k) * sizeof(float) : 0);
+  if (nc > (long long)(kNoAllocBytes / per_cell) || ctrl_bytes + per_cell * (size_t)nc + 256 > kNoAllocBytes)
     return DG_ERR_TOO_LARGE;
   g.nx = mesh->n[0];
   g.ny = mesh->n[1];
@@ -1029,9 +1076,16 @@ extern "C" int dg_rhs_noalloc(const dg_mesh* mesh, int order, double gamma, int 
   DG_TRY(noalloc_setup(dev, k, &scratch));
   Ctrl* ctrl = static_cast<Ctrl*>(scratch);
   void* fh = static_cast<unsigned char*>(scratch) + ctrl_bytes;
+  float* yf = nullptr;
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-  const Launchers L = launchers_for(k);
-  DG_CUDA(L.face(precision, y_dev, fh, g, s));
-  DG_CUDA(L.volume_rhs(precision, false, y_dev, fh, nullptr, g, R_dev, ctrl, s));
+  if (shadow) {
+    const size_t fh_bytes = (size_t)15 * Q * Q * tsize * (size_t)nc;
+    yf = reinterpret_cast<float*>(static_cast<unsigned char*>(fh) + ((fh_bytes + 255) & ~size_t(255)));
+    const long long n = (long long)5 * nmodes(k) * nc;
+    to_f32_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(y_dev, yf, n);
+    DG_CUDA(cudaGetLastError());
+  }
+  DG_CUDA(L.face(precision, y_dev, yf, fh, g, s));
+  DG_CUDA(L.volume_rhs(precision, false, y_dev, yf, fh, nullptr, g, R_dev, ctrl, s));
   return DG_OK;
 }

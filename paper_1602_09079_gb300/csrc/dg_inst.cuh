@@ -90,10 +90,10 @@ cudaError_t face_t(const double* y, void* fh, const Geo& g, cudaStream_t s) {
 // FP32 tiled kernels with constant-bank tables for degrees <= 2; degree 3
 // keeps the generic shared-memory kernels.
 
-cudaError_t face(int prec, const double* y, void* fh, const Geo& g, cudaStream_t s) {
+cudaError_t face(int prec, const double* y, const float* yf, void* fh, const Geo& g, cudaStream_t s) {
   if constexpr (kRegF32) {
     if (prec) {
-      face_flux_f32_kernel<KK><<<grid1(g.nc, 32), 96, 0, s>>>(y, static_cast<float*>(fh), g);
+      face_flux_f32_kernel<KK><<<grid1(g.nc, 32), 96, 0, s>>>(yf, static_cast<float*>(fh), g);
       return cudaGetLastError();
     }
   }
@@ -101,11 +101,11 @@ cudaError_t face(int prec, const double* y, void* fh, const Geo& g, cudaStream_t
 }
 
 template <int MODE, bool FORCE>
-cudaError_t vol_f32(const double* y, const void* fh, const void* field, const Geo& g, StageArgs st, double* R,
+cudaError_t vol_f32(const float* yf, const void* fh, const void* field, const Geo& g, StageArgs st, double* R,
                     Ctrl* ctrl, cudaStream_t s) {
   using CF = VolF32<KK>;
   volume_f32_kernel<KK, MODE, FORCE><<<grid1(g.nc, CF::C), CF::THREADS, CF::smem(FORCE), s>>>(
-      y, static_cast<const float*>(fh), static_cast<const float*>(field), tab_ptr<double>(), g, st, R, ctrl);
+      yf, static_cast<const float*>(fh), static_cast<const float*>(field), tab_ptr<double>(), g, st, R, ctrl);
   return cudaGetLastError();
 }
 
@@ -118,13 +118,13 @@ cudaError_t vol_t(const double* y, const void* fh, const void* field, const Geo&
   return cudaGetLastError();
 }
 
-cudaError_t volume_rhs(int prec, bool force, const double* y, const void* fh, const void* field, const Geo& g,
-                       double* R, Ctrl* ctrl, cudaStream_t s) {
+cudaError_t volume_rhs(int prec, bool force, const double* y, const float* yf, const void* fh, const void* field,
+                       const Geo& g, double* R, Ctrl* ctrl, cudaStream_t s) {
   StageArgs st{};
   if constexpr (kRegF32) {
     if (prec)
-      return force ? vol_f32<MODE_RHS, true>(y, fh, field, g, st, R, ctrl, s)
-                   : vol_f32<MODE_RHS, false>(y, fh, field, g, st, R, ctrl, s);
+      return force ? vol_f32<MODE_RHS, true>(yf, fh, field, g, st, R, ctrl, s)
+                   : vol_f32<MODE_RHS, false>(yf, fh, field, g, st, R, ctrl, s);
   }
   if (prec)
     return force ? vol_t<float, MODE_RHS, true>(y, fh, field, g, st, R, ctrl, s)
@@ -134,13 +134,13 @@ cudaError_t volume_rhs(int prec, bool force, const double* y, const void* fh, co
 }
 
 cudaError_t volume_stage(int prec, bool force, const void* fh, const void* field, const Geo& g, const double* ys,
-                         const double* y0, double* out, double a0, double b0, double dt, int* list, Ctrl* ctrl,
-                         cudaStream_t s) {
-  StageArgs st{ys, y0, out, a0, b0, dt, list};
+                         const double* y0, double* out, double a0, double b0, double dt, int* list, float* yf,
+                         Ctrl* ctrl, cudaStream_t s) {
+  StageArgs st{ys, y0, out, a0, b0, dt, list, yf};
   if constexpr (kRegF32) {
     if (prec)
-      return force ? vol_f32<MODE_STAGE, true>(ys, fh, field, g, st, nullptr, ctrl, s)
-                   : vol_f32<MODE_STAGE, false>(ys, fh, field, g, st, nullptr, ctrl, s);
+      return force ? vol_f32<MODE_STAGE, true>(yf, fh, field, g, st, nullptr, ctrl, s)
+                   : vol_f32<MODE_STAGE, false>(yf, fh, field, g, st, nullptr, ctrl, s);
   }
   if (prec)
     return force ? vol_t<float, MODE_STAGE, true>(ys, fh, field, g, st, nullptr, ctrl, s)
@@ -150,8 +150,8 @@ cudaError_t volume_stage(int prec, bool force, const void* fh, const void* field
 }
 
 cudaError_t limit_list(double* y, const int* list, const unsigned* count, const Geo& g, Ctrl* ctrl, int count_queued,
-                       cudaStream_t s) {
-  limit_list_kernel<KK><<<152, kThreads, 0, s>>>(y, list, count, tab_ptr<double>(), g, ctrl, count_queued);
+                       float* yf, cudaStream_t s) {
+  limit_list_kernel<KK><<<152, kThreads, 0, s>>>(y, list, count, tab_ptr<double>(), g, ctrl, count_queued, yf);
   return cudaGetLastError();
 }
 
@@ -176,18 +176,18 @@ constexpr int kResetCells = 32;
 
 template <typename T>
 cudaError_t reset_t(double* y, const Geo& g, double c2g, double inv_rho0, double* part, int* n_part, int* list,
-                    Ctrl* ctrl, cudaStream_t s) {
+                    Ctrl* ctrl, float* yf, cudaStream_t s) {
   unsigned nb = grid1(g.nc, kResetCells);
   *n_part = (int)nb;
   energy_reset_kernel<KK, T, kResetCells><<<nb, kThreads, 0, s>>>(y, tab_ptr<T>(), tab_ptr<double>(), g, c2g, inv_rho0,
-                                                                  part, list, ctrl);
+                                                                  part, list, ctrl, yf);
   return cudaGetLastError();
 }
 
 cudaError_t energy_reset(int prec, double* y, const Geo& g, double c2g, double inv_rho0, double* part, int* n_part,
-                         int* list, Ctrl* ctrl, cudaStream_t s) {
-  return prec ? reset_t<float>(y, g, c2g, inv_rho0, part, n_part, list, ctrl, s)
-              : reset_t<double>(y, g, c2g, inv_rho0, part, n_part, list, ctrl, s);
+                         int* list, Ctrl* ctrl, float* yf, cudaStream_t s) {
+  return prec ? reset_t<float>(y, g, c2g, inv_rho0, part, n_part, list, ctrl, yf, s)
+              : reset_t<double>(y, g, c2g, inv_rho0, part, n_part, list, ctrl, yf, s);
 }
 
 cudaError_t project(const double* f, double* y, const Geo& g, long long first, long long count, cudaStream_t s) {
@@ -216,6 +216,7 @@ Launchers DG_PASTE(launchers_k, DG_K)() {
   Launchers L;
   L.k = KK;
   L.upload = upload;
+  L.f32_shadow = kRegF32;
   L.face = face;
   L.volume_rhs = volume_rhs;
   L.volume_stage = volume_stage;

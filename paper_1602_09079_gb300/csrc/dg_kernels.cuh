@@ -42,7 +42,9 @@ struct StageArgs {
   const double* y0;  // y^(0) of the step
   double* out;       // stage output (may alias ys or y0; cells are CTA-private)
   double a0, b0, dt; // out = a0 y0 + b0 (ys - dt R(ys))
-  int* list;         // cells whose limiter screen failed (FP32 register path)
+  int* list;         // cells whose limiter screen failed
+  float* yf;         // FP32 shadow of the stage state (FP32 path): read for
+                     // this CTA's cells, then overwritten with the output
 };
 
 __device__ __forceinline__ void cell_xyz(long long c, const Geo& g, int& ix, int& iy, int& iz) {
@@ -283,14 +285,15 @@ namespace {
 __constant__ float c_tab32[Tab<3>::SIZE];
 }
 
-// Face fluxes, FP32: tiles of 32 consecutive cells, warp d computes the low
+// Face fluxes, FP32 (from the FP32 shadow of the state): tiles of 32
+// consecutive cells, warp d computes the low
 // face in direction d of each cell (left state = the lower neighbour's high
 // face, right state = the cell's own low face). Traces are sum-factorised:
 // the coefficients are first contracted with Pt_e(+-1) along the normal into
 // the tangential coefficients E[i][(a,b)], which then give the values at all
 // Q^2 face points through the tangential products (constant tables).
 template <int K, int D>
-__device__ __forceinline__ void face_f32_dir(const double* __restrict__ y, float* __restrict__ fh, const Geo& g,
+__device__ __forceinline__ void face_f32_dir(const float* __restrict__ yf, float* __restrict__ fh, const Geo& g,
                                              long long c, int ix, int iy, int iz) {
   using TB = Tab<K>;
   constexpr int N = TB::N, Q2 = TB::Q2, T = TB::T;
@@ -314,8 +317,8 @@ __device__ __forceinline__ void face_f32_dir(const double* __restrict__ y, float
         const float pr = c_tab32[TB::FEND + e];            // own cell: its low face, xi_d = -1
 #pragma unroll
         for (int i = 0; i < 5; ++i) {
-          EL[i * T + j] += (float)__ldg(y + (size_t)(i * N + m) * nc + cl) * pl;
-          ER[i * T + j] += (float)__ldg(y + (size_t)(i * N + m) * nc + c) * pr;
+          EL[i * T + j] += __ldg(yf + (size_t)(i * N + m) * nc + cl) * pl;
+          ER[i * T + j] += __ldg(yf + (size_t)(i * N + m) * nc + c) * pr;
         }
       }
   const float gamma = (float)g.gamma;
@@ -342,16 +345,16 @@ __device__ __forceinline__ void face_f32_dir(const double* __restrict__ y, float
 }
 
 template <int K>
-__global__ void __launch_bounds__(96, 6) face_flux_f32_kernel(const double* __restrict__ y, float* __restrict__ fh,
-                                                           Geo g) {
+__global__ void __launch_bounds__(96, 6) face_flux_f32_kernel(const float* __restrict__ yf, float* __restrict__ fh,
+                                                              Geo g) {
   const long long c = (long long)blockIdx.x * 32 + (threadIdx.x & 31);
   if (c >= g.nc) return;
   const int d = threadIdx.x >> 5;  // warp-uniform direction
   int ix, iy, iz;
   cell_xyz(c, g, ix, iy, iz);
-  if (d == 0) face_f32_dir<K, 0>(y, fh, g, c, ix, iy, iz);
-  else if (d == 1) face_f32_dir<K, 1>(y, fh, g, c, ix, iy, iz);
-  else face_f32_dir<K, 2>(y, fh, g, c, ix, iy, iz);
+  if (d == 0) face_f32_dir<K, 0>(yf, fh, g, c, ix, iy, iz);
+  else if (d == 1) face_f32_dir<K, 1>(yf, fh, g, c, ix, iy, iz);
+  else face_f32_dir<K, 2>(yf, fh, g, c, ix, iy, iz);
 }
 
 // Volume quadrature, FP32, tiled in two phases over a tile of C cells:
@@ -486,7 +489,7 @@ __device__ __forceinline__ void vol_f32_chunk(const float* sW, float* sF, float*
 // screen (cells failing it are queued for the full limiter).
 template <int K, int MODE, bool FORCE>
 __global__ void __launch_bounds__(VolF32<K>::THREADS, VolF32<K>::MINB) volume_f32_kernel(
-    const double* __restrict__ yin, const float* __restrict__ fh, const float* __restrict__ field,
+    const float* yfin, const float* __restrict__ fh, const float* __restrict__ field,
     const double* __restrict__ tab64, Geo g, StageArgs st, double* __restrict__ R, Ctrl* ctrl) {
   using TB = Tab<K>;
   using CF = VolF32<K>;
@@ -500,11 +503,11 @@ __global__ void __launch_bounds__(VolF32<K>::THREADS, VolF32<K>::MINB) volume_f3
   const long long nc = g.nc;
   const long long c0 = (long long)blockIdx.x * C;
   const int tid = threadIdx.x;
-  const double* ysrc = (MODE == MODE_STAGE) ? st.ys : yin;
+  const float* ysrc = (MODE == MODE_STAGE) ? st.yf : yfin;
   for (int it = tid; it < 5 * N * C; it += CF::THREADS) {
     const int c = it % C, r = it / C;
     const long long cell = c0 + c;
-    sW[r * C + c] = cell < nc ? (float)ysrc[(size_t)r * nc + cell] : (r == 0 ? 1.f : 0.f);
+    sW[r * C + c] = cell < nc ? ysrc[(size_t)r * nc + cell] : (r == 0 ? 1.f : 0.f);
   }
   __syncthreads();
   const float idx[3] = {(float)g.inv_dx[0], (float)g.inv_dx[1], (float)g.inv_dx[2]};
@@ -543,7 +546,8 @@ __global__ void __launch_bounds__(VolF32<K>::THREADS, VolF32<K>::MINB) volume_f3
     }
     return;
   }
-  double sabs = 0.0, mean = 0.0;
+  double mean = 0.0;
+  float sabsf = 0.f;
   bool finite = true;
   if (live) {
 #pragma unroll
@@ -551,11 +555,17 @@ __global__ void __launch_bounds__(VolF32<K>::THREADS, VolF32<K>::MINB) volume_f3
       const size_t a = (size_t)(i * N + l) * nc + cell;
       const double v = st.a0 * __ldcg(st.y0 + a) + st.b0 * (__ldcg(st.ys + a) + st.dt * (double)acc[l]);
       st.out[a] = v;
+      const float vf = (float)v;
+      st.yf[a] = vf;
       finite &= isfinite(v);
       if (l == 0) mean = v;
-      else sabs += fabs(v) * __ldg(tab64 + TB::LMAX + l);
+      else sabsf += fabsf(vf) * c_tab32[TB::LMAX + l];
     }
   }
+  // the screen's excursion sums are taken in FP32 from the rounded values
+  // (relative error below 1e-6); a relative margin of 1e-5 keeps the test a
+  // sufficient one
+  const double sabs = (double)sabsf * (1.0 + 1e-5);
   sM[i * C + c] = finite ? mean : __longlong_as_double(0x7ff8000000000000LL);  // NaN marks non-finite
   sA[i * C + c] = sabs;
   __syncthreads();
@@ -580,17 +590,23 @@ __global__ void __launch_bounds__(VolF32<K>::THREADS, VolF32<K>::MINB) volume_f3
 template <int K>
 __global__ void __launch_bounds__(kThreads) limit_list_kernel(double* __restrict__ y, const int* __restrict__ list,
                                                               const unsigned* count, const double* __restrict__ tab64,
-                                                              Geo g, Ctrl* ctrl, int count_queued) {
+                                                              Geo g, Ctrl* ctrl, int count_queued,
+                                                              float* __restrict__ yf) {
+  constexpr int N = nmodes(K);
   const unsigned n = *count;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     atomicAdd(&ctrl->n_full_total, (unsigned long long)n);
     if (count_queued) atomicAdd(&ctrl->n_queued_total, (unsigned long long)n);
   }
   unsigned e = 0;
-  for (unsigned i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads)
-    limit_cell<K>(y + list[i], g.nc, tab64, g.gamma, g.eps_rho, g.eps_p, &e);
+  for (unsigned i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) {
+    const long long cell = list[i];
+    if (limit_cell<K>(y + cell, g.nc, tab64, g.gamma, g.eps_rho, g.eps_p, &e) && yf)
+      for (int r = 0; r < 5 * N; ++r) yf[(size_t)r * g.nc + cell] = (float)y[(size_t)r * g.nc + cell];
+  }
   if (e) atomicOr(&ctrl->err, e);
 }
+
 
 // screen[c] = 1 when cell c fails the limiter screen (capture of training data)
 template <int K>
@@ -696,7 +712,8 @@ template <int K, typename T, int C>
 __global__ void __launch_bounds__(kThreads) energy_reset_kernel(double* __restrict__ y, const T* __restrict__ tab,
                                                                 const double* __restrict__ tab64, Geo g, double c2g,
                                                                 double inv_rho0, double* __restrict__ part,
-                                                                int* __restrict__ list, Ctrl* ctrl) {
+                                                                int* __restrict__ list, Ctrl* ctrl,
+                                                                float* __restrict__ yf) {
   using TB = Tab<K>;
   constexpr int N = TB::N, Q3 = TB::Q3;
   __shared__ T sW[4 * N * C];
@@ -787,7 +804,10 @@ __global__ void __launch_bounds__(kThreads) energy_reset_kernel(double* __restri
   for (int it = tid; it < N * C; it += kThreads) {
     const int c = it % C, l = it / C;
     const long long cell = c0 + c;
-    if (cell < nc) y[(size_t)(4 * N + l) * nc + cell] = sEn[l * C + c];
+    if (cell < nc) {
+      y[(size_t)(4 * N + l) * nc + cell] = sEn[l * C + c];
+      if (yf) yf[(size_t)(4 * N + l) * nc + cell] = (float)sEn[l * C + c];
+    }
   }
 }
 

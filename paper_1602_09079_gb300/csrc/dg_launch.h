@@ -14,20 +14,24 @@ struct Launchers {
   int k;
   // copy the degree's tables (FP64 and FP32 copies) to the current device
   cudaError_t (*upload)(const double* h64, const float* h32);
+  // true when the FP32 path reads an FP32 shadow of the state (yf) instead
+  // of the FP64 state
+  bool f32_shadow;
   // one HLLC flux per face point; fh holds T = double (prec 0) or float (prec 1)
-  cudaError_t (*face)(int prec, const double* y, void* fh, const Geo& g, cudaStream_t s);
+  cudaError_t (*face)(int prec, const double* y, const float* yf, void* fh, const Geo& g, cudaStream_t s);
   // R(y) written in FP64, state layout
-  cudaError_t (*volume_rhs)(int prec, bool force, const double* y, const void* fh, const void* field,
-                            const Geo& g, double* R, Ctrl* ctrl, cudaStream_t s);
+  cudaError_t (*volume_rhs)(int prec, bool force, const double* y, const float* yf, const void* fh,
+                            const void* field, const Geo& g, double* R, Ctrl* ctrl, cudaStream_t s);
   // SSP-RK3 stage combination + limiter screen: cells failing the screen are
   // queued in list / ctrl->n_flag (ctrl->n_flag must be 0 on entry)
   cudaError_t (*volume_stage)(int prec, bool force, const void* fh, const void* field, const Geo& g,
                               const double* ys, const double* y0, double* out, double a0, double b0,
-                              double dt, int* list, Ctrl* ctrl, cudaStream_t s);
+                              double dt, int* list, float* yf, Ctrl* ctrl, cudaStream_t s);
   // full limiter on the *count cells of list (count_queued: also add them
-  // to the screen-failure total, i.e. no indicator filtered the list)
+  // to the screen-failure total, i.e. no indicator filtered the list); yf
+  // (nullable): FP32 shadow updated for the cells the limiter changes
   cudaError_t (*limit_list)(double* y, const int* list, const unsigned* count, const Geo& g, Ctrl* ctrl,
-                            int count_queued, cudaStream_t s);
+                            int count_queued, float* yf, cudaStream_t s);
   // screen[c] = 1 if cell c fails the limiter screen
   cudaError_t (*screen)(const double* y, uint8_t* screen, const Geo& g, cudaStream_t s);
   cudaError_t (*limit)(double* y, int8_t* flags, const Geo& g, Ctrl* ctrl, cudaStream_t s);
@@ -35,7 +39,7 @@ struct Launchers {
   // returns the number of partial sums written to part; cells failing the
   // limiter screen afterwards are queued in list / ctrl->n_flag (0 on entry)
   cudaError_t (*energy_reset)(int prec, double* y, const Geo& g, double c2g, double inv_rho0, double* part,
-                              int* n_part, int* list, Ctrl* ctrl, cudaStream_t s);
+                              int* n_part, int* list, Ctrl* ctrl, float* yf, cudaStream_t s);
   // projection of the cells first .. first + count - 1
   cudaError_t (*project)(const double* f, double* y, const Geo& g, long long first, long long count, cudaStream_t s);
   cudaError_t (*forcing_field)(int prec, void* field, const double* modes, int n_modes, const Geo& g,

@@ -178,3 +178,103 @@ def test_training_on_gpu_reduces_loss(dg):
     acc = float(((logits > 0).float() == yd).float().mean())
     assert losses[1] < 0.3 * losses[0], losses
     assert acc > 0.95, acc
+
+
+def _snapshots(dg, fn, n, steps, every, courant=0.15):
+    """FP64 runs of the solver with the plain limiter; every `every` steps,
+    capture (features, label) of the cells that fail the limiter's screen,
+    the label being the plain indicator's flag."""
+    import torch
+    order = 3
+    nf, F, npar, work = dg.dg_indicator_sizes(order)
+    s = dg.Solver((n, n, n), order, syn.GAMMA)
+    s.project_fn(fn)
+    X = torch.empty((s.ncells, F), dtype=torch.bfloat16, device="cuda")
+    fl = torch.empty(s.ncells, dtype=torch.int8, device="cuda")
+    sc = torch.empty(s.ncells, dtype=torch.uint8, device="cuda")
+    xs, ys = [], []
+    for it in range(steps):
+        dt = s.cfl_dt(courant)
+        s.step(dt)
+        if it % every == every - 1:
+            dg.dg_indicator_capture(s.ctx, dt, X, fl, sc)
+            m = sc.bool()
+            assert int(((fl != 0) & ~m).sum()) == 0  # the screen is a sufficient test
+            xs.append(X[m].clone())
+            ys.append((fl[m] != 0).float())
+    return torch.cat(xs), torch.cat(ys)
+
+
+def test_trained_indicator_gain_over_plain_screen(dg):
+    """The troubled-cell network, trained on the GPU with the library's own
+    backward and Adam kernels from labels of the plain limiter's indicator,
+    gates the full limiter: on held-out supersonic turbulence and Sod tubes it
+    sends fewer screen-failing cells to the full limiter than the method
+    without it (which evaluates all of them), at a recall (judged by the plain
+    indicator) of at least 95%; a gated held-out run stays positive."""
+    import torch
+    order, n = 3, 24
+    nf, F, npar, work = dg.dg_indicator_sizes(order)
+
+    def data(specs):
+        xs, ys = [], []
+        for kind, seed, mach in specs:
+            if kind == "super":
+                fn = syn.supersonic_velocity(seed, mach, syn.GAMMA)
+                x, y = _snapshots(dg, fn, n, 240, 30)
+            else:
+                fn, _ = syn.sod_tube(seed, syn.GAMMA)
+                x, y = _snapshots(dg, fn, n, 120, 20)
+            xs.append(x)
+            ys.append(y)
+        return torch.cat(xs), torch.cat(ys)
+
+    Xtr, ytr = data([("super", 1, 2.0), ("super", 2, 2.5), ("super", 3, 3.0), ("super", 4, 2.5),
+                     ("sod", 1, 0), ("sod", 2, 0)])
+    Xva, yva = data([("super", 9, 2.5), ("sod", 6, 0)])
+    Xte, yte = data([("super", 7, 2.5), ("sod", 5, 0)])
+    assert float(ytr.sum()) > 100 and float(yte.sum()) > 50
+    P = torch.from_numpy(flat(rand_params(F, 70))).cuda()
+    m = torch.zeros_like(P)
+    v = torch.zeros_like(P)
+    G = torch.zeros(npar + 1, dtype=torch.float32, device="cuda")
+    Wk = torch.empty(work, dtype=torch.uint8, device="cuda")
+    pos = float(ytr.sum())
+    pw = max(1.0, (len(ytr) - pos) / pos)
+    first = None
+    for step in range(1, 1201):
+        dg.dg_indicator_backward(order, Xtr, ytr, len(ytr), pw, P, G, Wk, work, 0)
+        if step == 1:
+            first = float(G[npar])
+        dg.dg_indicator_adam(P, m, v, G, npar, 3e-3, 0.9, 0.999, 1e-8, step, 0)
+    last = float(G[npar])
+    assert last < 0.3 * first, (first, last)
+
+    def prob(X):
+        out = torch.empty(len(X), dtype=torch.float32, device="cuda")
+        dg.dg_indicator_forward(order, X, len(X), P, out, 0)
+        return torch.sigmoid(out)
+
+    # threshold from the validation runs: 99% of their troubled cells pass
+    thr = float(torch.quantile(prob(Xva)[yva > 0], 0.01))
+    pte = prob(Xte)
+    sel = pte >= thr
+    recall = float((sel & (yte > 0)).sum()) / float((yte > 0).sum())
+    evaluated = float(sel.float().mean())
+    print(f"indicator: threshold {thr:.3g}, held-out recall {recall:.4f}, "
+          f"fraction of screen-failing cells sent to the full limiter {evaluated:.3f}")
+    assert recall >= 0.95
+    assert evaluated < 0.95
+    # gated run on a held-out Sod tube: positivity holds, less full-limiter work
+    fn, _ = syn.sod_tube(5, syn.GAMMA)
+    counts = {}
+    for gate in (False, True):
+        s = dg.Solver((n, n, n), order, syn.GAMMA)
+        s.project_fn(fn)
+        if gate:
+            dg.dg_set_indicator(s.ctx, P, max(min(thr, 0.999), 1e-12))
+        for _ in range(100):
+            s.step(s.cfl_dt(0.15))
+        s.check()
+        counts[gate] = dg.dg_limiter_counts(s.ctx)
+    assert counts[True][1] < counts[False][1], counts
