@@ -47,7 +47,9 @@ class Params(C.Structure):
     _fields_ = [("k", C.c_int), ("n", C.c_int * 3), ("L", C.c_double * 3),
                 ("gamma", C.c_double), ("eps_rho", C.c_double), ("eps_p", C.c_double),
                 ("n_force", C.c_int), ("force_n", C.POINTER(C.c_int32)),
-                ("force_a", C.POINTER(C.c_double))]
+                ("force_a", C.POINTER(C.c_double)), ("flux", C.c_int)]
+
+FLUX_HLLC, FLUX_EXACT = 0, 1
 
 
 def _load():
@@ -72,6 +74,9 @@ def _load():
                 "orc_eval": (None, [P, dp, C.c_long, dp, dp]),
                 "orc_euler_flux": (None, [C.c_int, C.c_double, dp, dp]),
                 "orc_hllc": (None, [C.c_int, C.c_double, dp, dp, dp]),
+                "orc_exact_star": (C.c_int, [C.c_double, dp, dp, dp, dp]),
+                "orc_exact_sample": (C.c_int, [C.c_double, dp, dp, C.c_double, dp]),
+                "orc_exact_flux": (C.c_int, [C.c_int, C.c_double, dp, dp, dp]),
                 "orc_rhs": (C.c_int, [P, dp, dp]),
                 "orc_rhs_cells": (C.c_int, [P, dp, C.c_long, i64p, dp]),
                 "orc_forcing_accel": (None, [P, C.c_long, dp, dp]),
@@ -151,6 +156,27 @@ def hllc(direction: int, gamma: float, UL, UR):
     return F
 
 
+def exact_star(gamma: float, WL, WR):
+    """(status, p*, u*) of the exact Riemann solution for primitive states
+    W = (rho, u, p); status 1 = vacuum between two rarefactions."""
+    ps, us = np.zeros(1), np.zeros(1)
+    st = _load().orc_exact_star(gamma, _dp(_f64(WL)), _dp(_f64(WR)), _dp(ps), _dp(us))
+    return st, float(ps[0]), float(us[0])
+
+
+def exact_sample(gamma: float, WL, WR, s: float):
+    W = np.zeros(3)
+    st = _load().orc_exact_sample(gamma, _dp(_f64(WL)), _dp(_f64(WR)), float(s), _dp(W))
+    return st, W
+
+
+def exact_flux(direction: int, gamma: float, UL, UR):
+    F = np.zeros(5)
+    st = _load().orc_exact_flux(direction, gamma, _dp(_f64(UL)), _dp(_f64(UR)), _dp(F))
+    assert st >= 0, st
+    return F
+
+
 def pressure_tau(gamma: float, qbar, q, eps: float):
     it = C.c_int(0)
     tau = _load().orc_pressure_tau(gamma, _dp(_f64(qbar)), _dp(_f64(q)), eps, C.byref(it))
@@ -165,7 +191,7 @@ class Oracle:
     """One periodic Cartesian mesh, degree k, ideal gas gamma, optional
     forcing modes; every method takes and returns canonical-layout arrays."""
 
-    def __init__(self, n, k, gamma, L=(1.0, 1.0, 1.0), eps_rho=1e-12, eps_p=1e-12):
+    def __init__(self, n, k, gamma, L=(1.0, 1.0, 1.0), eps_rho=1e-12, eps_p=1e-12, flux=FLUX_HLLC):
         self.n = tuple(int(v) for v in n)
         self.k = int(k)
         self.N = nmodes(self.k)
@@ -184,6 +210,7 @@ class Oracle:
         self._p.eps_rho = eps_rho
         self._p.eps_p = eps_p
         self._p.n_force = 0
+        self._p.flux = int(flux)
         self._p.force_n = self._force_n.ctypes.data_as(C.POINTER(C.c_int32))
         self._p.force_a = _dp(self._force_a)
 

@@ -315,6 +315,175 @@ void orc_forcing_accel(const orc_params* p, long n, const double* xyz, double* a
 
 /* ------------------------------------------------------------------- R(w) */
 
+/* ------------------------------------------------ exact Riemann solver */
+
+/* The exact solution of the one-dimensional Riemann problem of the Euler
+ * equations for an ideal gas, the "exact" flux option of Sect. 2.3 (after
+ * Eq. dg:eqn:surface_int), built the standard way (Toro, "Riemann Solvers
+ * and Numerical Methods for Fluid Dynamics", Ch. 4):
+ *  - across the wave of side K, the velocity change as a function of the
+ *    star pressure p is f_K(p): the Rankine-Hugoniot shock branch for
+ *    p > p_K, the isentropic rarefaction branch (Riemann invariant) for
+ *    p <= p_K;
+ *  - p* is the root of f(p) = f_L(p) + f_R(p) + u_R - u_L (increasing and
+ *    concave), found by Newton's method from the adaptive estimate (the
+ *    primitive-variable linearisation when the pressures are close, else the
+ *    two-rarefaction or two-shock approximation);
+ *  - u* = (u_L + u_R + f_R(p*) - f_L(p*)) / 2;
+ *  - the state at x/t = s follows from the wave pattern (shock speeds from
+ *    the jump conditions, rarefaction fans from the self-similar solution). */
+
+static void exact_fk(double gamma, double p, double rk, double pk, double ck, double* f, double* df) {
+  if (p > pk) {
+    double A = 2.0 / ((gamma + 1.0) * rk);
+    double B = (gamma - 1.0) / (gamma + 1.0) * pk;
+    double q = sqrt(A / (p + B));
+    *f = (p - pk) * q;
+    *df = q * (1.0 - 0.5 * (p - pk) / (p + B));
+  } else {
+    double r = pow(p / pk, (gamma - 1.0) / (2.0 * gamma));
+    *f = 2.0 * ck / (gamma - 1.0) * (r - 1.0);
+    *df = ck * r / (gamma * p);
+  }
+}
+
+int orc_exact_star(double gamma, const double WL[3], const double WR[3], double* pstar, double* ustar) {
+  double rL = WL[0], uL = WL[1], pL = WL[2], rR = WR[0], uR = WR[1], pR = WR[2];
+  double cL = sqrt(gamma * pL / rL), cR = sqrt(gamma * pR / rR);
+  double du = uR - uL;
+  if (2.0 * (cL + cR) / (gamma - 1.0) <= du) {
+    *pstar = 0.0;
+    *ustar = 0.0;
+    return 1;
+  }
+  /* starting value */
+  double ppv = 0.5 * (pL + pR) - 0.125 * du * (rL + rR) * (cL + cR);
+  if (ppv < 0.0) ppv = 0.0;
+  double pmin = fmin(pL, pR), pmax = fmax(pL, pR);
+  double p;
+  if (pmax / pmin <= 2.0 && ppv >= pmin && ppv <= pmax) {
+    p = ppv;
+  } else if (ppv < pmin) {
+    double z = (gamma - 1.0) / (2.0 * gamma);
+    p = pow((cL + cR - 0.5 * (gamma - 1.0) * du) / (cL / pow(pL, z) + cR / pow(pR, z)), 1.0 / z);
+  } else {
+    double gL = sqrt(2.0 / ((gamma + 1.0) * rL) / (ppv + (gamma - 1.0) / (gamma + 1.0) * pL));
+    double gR = sqrt(2.0 / ((gamma + 1.0) * rR) / (ppv + (gamma - 1.0) / (gamma + 1.0) * pR));
+    p = (gL * pL + gR * pR - du) / (gL + gR);
+  }
+  const double tiny = 1e-14 * pmin;
+  if (!(p > tiny)) p = tiny;
+  int it;
+  for (it = 0; it < 100; ++it) {
+    double fL, dfL, fR, dfR;
+    exact_fk(gamma, p, rL, pL, cL, &fL, &dfL);
+    exact_fk(gamma, p, rR, pR, cR, &fR, &dfR);
+    double pn = p - (fL + fR + du) / (dfL + dfR);
+    if (!(pn > tiny)) pn = tiny;
+    double change = fabs(pn - p);
+    p = pn;
+    if (change <= 1e-14 * p) break;
+  }
+  if (it == 100 || !isfinite(p)) return ORC_ERR_NEWTON;
+  double fL, dfL, fR, dfR;
+  exact_fk(gamma, p, rL, pL, cL, &fL, &dfL);
+  exact_fk(gamma, p, rR, pR, cR, &fR, &dfR);
+  *pstar = p;
+  *ustar = 0.5 * (uL + uR) + 0.5 * (fR - fL);
+  return ORC_OK;
+}
+
+/* state inside the rarefaction fan of side K (sgn = +1 left, -1 right) at x/t = s */
+static void exact_fan(double gamma, double rk, double uk, double pk, double ck, double sgn, double s, double W[3]) {
+  double c = 2.0 / (gamma + 1.0) * (ck + sgn * 0.5 * (gamma - 1.0) * (uk - s));
+  W[1] = s + sgn * c;
+  W[0] = rk * pow(c / ck, 2.0 / (gamma - 1.0));
+  W[2] = pk * pow(c / ck, 2.0 * gamma / (gamma - 1.0));
+}
+
+/* side of the contact the sample lies on: 0 left, 1 right (returned through
+ * *side when non-NULL) */
+static int exact_sample_side(double gamma, const double WL[3], const double WR[3], double s, double W[3], int* side) {
+  double rL = WL[0], uL = WL[1], pL = WL[2], rR = WR[0], uR = WR[1], pR = WR[2];
+  double cL = sqrt(gamma * pL / rL), cR = sqrt(gamma * pR / rR);
+  double ps, us;
+  int st = orc_exact_star(gamma, WL, WR, &ps, &us);
+  if (st < 0) return st;
+  double g1 = (gamma - 1.0) / (2.0 * gamma), g2 = (gamma + 1.0) / (2.0 * gamma), g6 = (gamma - 1.0) / (gamma + 1.0);
+  if (st == 1) {  /* two rarefactions and a vacuum between their tails */
+    double sL = uL + 2.0 * cL / (gamma - 1.0), sR = uR - 2.0 * cR / (gamma - 1.0);
+    if (s <= uL - cL) { W[0] = rL; W[1] = uL; W[2] = pL; if (side) *side = 0; }
+    else if (s < sL) { exact_fan(gamma, rL, uL, pL, cL, 1.0, s, W); if (side) *side = 0; }
+    else if (s <= sR) { W[0] = 0.0; W[1] = 0.5 * (sL + sR); W[2] = 0.0; if (side) *side = s <= 0.5 * (sL + sR) ? 0 : 1; }
+    else if (s < uR + cR) { exact_fan(gamma, rR, uR, pR, cR, -1.0, s, W); if (side) *side = 1; }
+    else { W[0] = rR; W[1] = uR; W[2] = pR; if (side) *side = 1; }
+    return 1;
+  }
+  if (s <= us) {
+    if (side) *side = 0;
+    if (ps > pL) {
+      double SL = uL - cL * sqrt(g2 * ps / pL + g1);
+      if (s <= SL) { W[0] = rL; W[1] = uL; W[2] = pL; }
+      else { W[0] = rL * (ps / pL + g6) / (g6 * ps / pL + 1.0); W[1] = us; W[2] = ps; }
+    } else {
+      double cs = cL * pow(ps / pL, g1);
+      if (s <= uL - cL) { W[0] = rL; W[1] = uL; W[2] = pL; }
+      else if (s > us - cs) { W[0] = rL * pow(ps / pL, 1.0 / gamma); W[1] = us; W[2] = ps; }
+      else exact_fan(gamma, rL, uL, pL, cL, 1.0, s, W);
+    }
+  } else {
+    if (side) *side = 1;
+    if (ps > pR) {
+      double SR = uR + cR * sqrt(g2 * ps / pR + g1);
+      if (s >= SR) { W[0] = rR; W[1] = uR; W[2] = pR; }
+      else { W[0] = rR * (ps / pR + g6) / (g6 * ps / pR + 1.0); W[1] = us; W[2] = ps; }
+    } else {
+      double cs = cR * pow(ps / pR, g1);
+      if (s >= uR + cR) { W[0] = rR; W[1] = uR; W[2] = pR; }
+      else if (s < us + cs) { W[0] = rR * pow(ps / pR, 1.0 / gamma); W[1] = us; W[2] = ps; }
+      else exact_fan(gamma, rR, uR, pR, cR, -1.0, s, W);
+    }
+  }
+  return ORC_OK;
+}
+
+int orc_exact_sample(double gamma, const double WL[3], const double WR[3], double s, double W[3]) {
+  return exact_sample_side(gamma, WL, WR, s, W, NULL);
+}
+
+int orc_exact_flux(int dir, double gamma, const double* UL, const double* UR, double* F) {
+  const double* U[2] = {UL, UR};
+  double W[2][3], vel[2][3];
+  for (int s = 0; s < 2; ++s) {
+    for (int a = 0; a < 3; ++a) vel[s][a] = U[s][1 + a] / U[s][0];
+    W[s][0] = U[s][0];
+    W[s][1] = vel[s][dir];
+    W[s][2] = pressure(gamma, U[s]);
+  }
+  double Wf[3];
+  int side = 0;
+  int st = exact_sample_side(gamma, W[0], W[1], 0.0, Wf, &side);
+  if (st < 0) {
+    for (int i = 0; i < 5; ++i) F[i] = NAN;
+    return st;
+  }
+  double rho = Wf[0], un = Wf[1], p = Wf[2];
+  double v[3];
+  for (int a = 0; a < 3; ++a) v[a] = a == dir ? un : vel[side][a];
+  double E = p / (gamma - 1.0) + 0.5 * rho * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+  F[0] = rho * un;
+  for (int a = 0; a < 3; ++a) F[1 + a] = rho * un * v[a] + (a == dir ? p : 0.0);
+  F[4] = (E + p) * un;
+  return ORC_OK;
+}
+
+/* numerical flux of Sect. 2.3 selected by p->flux */
+static int num_flux(const orc_params* p, int dir, const double* UL, const double* UR, double* F) {
+  if (p->flux == ORC_FLUX_EXACT) return orc_exact_flux(dir, p->gamma, UL, UR, F) < 0 ? ORC_ERR_NEWTON : ORC_OK;
+  orc_hllc(dir, p->gamma, UL, UR, F);
+  return ORC_OK;
+}
+
 /* dw/dt of one cell:
  *   dw_l/dt = sum_a 1/(4 dx_a) [ sum_{q in G^3} F_a(U_q) dphi_l/dxi_a(xi_q) om_q
  *             - sum_{s=+-1} s sum_{q in face(a,s)} Fhat_a phi_l(xi_{a=s,q}) om_q ]
@@ -323,7 +492,8 @@ void orc_forcing_accel(const orc_params* p, long n, const double* xyz, double* a
  * Eq. dg:eqn:surface_int divided by |K| = dx dy dz, with the outward normal of
  * each face written as the sign s; source from the forcing integral of
  * Sect. 3.1 (momentum rho a, energy m.a). */
-static void cell_dwdt(const orc_params* p, const double* w, long cell, double* dwdt) {
+static int cell_dwdt(const orc_params* p, const double* w, long cell, double* dwdt) {
+  int status = ORC_OK;
   int k = p->k, Q = k + 1, N = orc_nmodes(k);
   double g[MAXQ], gw[MAXQ];
   orc_gauss(Q, g, gw);
@@ -389,29 +559,30 @@ static void cell_dwdt(const orc_params* p, const double* w, long cell, double* d
           orc_basis(k, xn, phin, NULL);
           eval_at(k, wK, phio, Uo);
           eval_at(k, wN, phin, Un);
-          if (s > 0)
-            orc_hllc(al, p->gamma, Uo, Un, Fh);
-          else
-            orc_hllc(al, p->gamma, Un, Uo, Fh);
+          int fs = s > 0 ? num_flux(p, al, Uo, Un, Fh) : num_flux(p, al, Un, Uo, Fh);
+          if (fs != ORC_OK) status = fs;
           for (int i = 0; i < 5; ++i)
             for (int l = 0; l < N; ++l)
               dwdt[i * N + l] -= s * Fh[i] * phio[l] * om2 / (4.0 * dx[al]);
         }
     }
   }
+  return status;
 }
 
 int orc_rhs(const orc_params* p, const double* w, double* R) {
   if (check_params(p)) return ORC_ERR_ARG;
   int N = orc_nmodes(p->k);
   long nc = ncells(p);
-#pragma omp parallel for schedule(dynamic, 16)
+  int status = ORC_OK;
+#pragma omp parallel for schedule(dynamic, 16) reduction(min : status)
   for (long c = 0; c < nc; ++c) {
     double d[5 * MAXN];
-    cell_dwdt(p, w, c, d);
+    int st = cell_dwdt(p, w, c, d);
+    if (st < status) status = st;
     for (int j = 0; j < 5 * N; ++j) R[c * 5 * N + j] = -d[j];
   }
-  return ORC_OK;
+  return status;
 }
 
 int orc_rhs_cells(const orc_params* p, const double* w, long n_cells, const int64_t* cells, double* R) {
@@ -420,13 +591,15 @@ int orc_rhs_cells(const orc_params* p, const double* w, long n_cells, const int6
   long nc = ncells(p);
   for (long i = 0; i < n_cells; ++i)
     if (cells[i] < 0 || cells[i] >= nc) return ORC_ERR_ARG;
-#pragma omp parallel for schedule(dynamic, 4)
+  int status = ORC_OK;
+#pragma omp parallel for schedule(dynamic, 4) reduction(min : status)
   for (long i = 0; i < n_cells; ++i) {
     double d[5 * MAXN];
-    cell_dwdt(p, w, cells[i], d);
+    int st = cell_dwdt(p, w, cells[i], d);
+    if (st < status) status = st;
     for (int j = 0; j < 5 * N; ++j) R[i * 5 * N + j] = -d[j];
   }
-  return ORC_OK;
+  return status;
 }
 
 /* ---------------------------------------------------------------- limiter */
@@ -634,7 +807,11 @@ int orc_step(const orc_params* p, double* w, double dt) {
   for (int s = 0; s < 3 && st >= ORC_OK; ++s) {
     if (s > 0) st = orc_limit(p, ys, NULL, NULL);
     if (st < ORC_OK && st != ORC_ERR_NEWTON) break;
-    orc_rhs(p, ys, R);
+    int sr = orc_rhs(p, ys, R);
+    if (sr != ORC_OK) {
+      st = sr;
+      break;
+    }
     for (long j = 0; j < len; ++j) ys[j] = a0[s] * y0[j] + b0[s] * (ys[j] - dt * R[j]);
   }
   if (st >= ORC_OK || st == ORC_ERR_NEWTON) {

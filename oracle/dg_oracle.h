@@ -45,7 +45,10 @@ typedef struct {
   int n_force;        /* number of forcing Fourier modes (0 = none) */
   const int32_t* force_n;   /* 3*n_force integer wave vectors n, k = 2 pi n / L */
   const double* force_a;    /* 6*n_force: Re a_x,a_y,a_z, Im a_x,a_y,a_z */
+  int flux;           /* numerical flux: ORC_FLUX_HLLC or ORC_FLUX_EXACT */
 } orc_params;
+
+enum { ORC_FLUX_HLLC = 0, ORC_FLUX_EXACT = 1 };
 
 int orc_nmodes(int k);
 void orc_mode_exponents(int k, int32_t* uvw /* 3*N */);
@@ -65,6 +68,18 @@ void orc_eval(const orc_params* p, const double* w, long cell, const double xi[3
 
 void orc_euler_flux(int dir, double gamma, const double* U, double* F);
 void orc_hllc(int dir, double gamma, const double* UL, const double* UR, double* F);
+
+/* Exact Riemann solver, the other flux Sect. 2.3 allows after Eq.
+ * dg:eqn:surface_int. Primitive states W = (rho, u_normal, p).
+ * orc_exact_star: star pressure and velocity; returns ORC_OK, 1 when the
+ * two rarefactions open a vacuum (p* = 0, u* undefined), ORC_ERR_NEWTON when
+ * the iteration does not converge in 100 steps.
+ * orc_exact_sample: the self-similar solution at x/t = s (status as above).
+ * orc_exact_flux: Godunov flux across a face with normal +e_dir from the
+ * solution at x/t = 0; tangential velocities from the side of the contact. */
+int orc_exact_star(double gamma, const double WL[3], const double WR[3], double* pstar, double* ustar);
+int orc_exact_sample(double gamma, const double WL[3], const double WR[3], double s, double W[3]);
+int orc_exact_flux(int dir, double gamma, const double* UL, const double* UR, double* F);
 
 /* R(w) for all cells (Eqs. dg:eqn:volume_int, dg:eqn:surface_int) */
 int orc_rhs(const orc_params* p, const double* w, double* R);
