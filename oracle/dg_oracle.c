@@ -378,7 +378,12 @@ int orc_exact_star(double gamma, const double WL[3], const double WR[3], double*
     double fL, dfL, fR, dfR;
     exact_fk(gamma, p, rL, pL, cL, &fL, &dfL);
     exact_fk(gamma, p, rR, pR, cR, &fR, &dfR);
-    double pn = p - (fL + fR + du) / (dfL + dfR);
+    double f = fL + fR + du;
+    /* converged: the residual is at the rounding level of its terms (near a
+     * vacuum the root is so ill-conditioned that the step itself stays
+     * above 1e-14 p), else the relative step is below 1e-14 */
+    if (fabs(f) <= 1e-15 * (fabs(fL) + fabs(fR) + fabs(du))) break;
+    double pn = p - f / (dfL + dfR);
     if (!(pn > tiny)) pn = tiny;
     double change = fabs(pn - p);
     p = pn;

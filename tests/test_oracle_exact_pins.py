@@ -43,6 +43,7 @@ CASES = [  # (WL, WR): shock tube, two rarefactions, two shocks, strong shock, m
     ((1.0, 0.0, 800.0), (1.0, 0.0, 0.02)),
     ((0.5, 0.3, 2.0), (1.5, -0.7, 0.3)),
     ((1.0, -3.5, 0.5), (0.8, 3.6, 0.45)),
+    ((1.0, -3.7, 0.4), (1.0, 3.7, 0.4)),  # two rarefactions just short of a vacuum
 ]
 
 
