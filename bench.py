@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--n", type=int, default=128, help="cells per axis")
     ap.add_argument("--order", type=int, default=3)
     ap.add_argument("--courant", type=float, default=0.3)
+    ap.add_argument("--flux", choices=["hllc", "exact"], default="hllc",
+                    help="numerical flux: HLLC or the exact Riemann solver")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--err-steps", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -72,7 +74,9 @@ def workload_config(args, precision):
         "workload": (f"driven subsonic turbulence, periodic {n}^3 box, order {args.order} "
                      f"(degree {args.order - 1}), gamma 5/3, warm start rms Mach {MACH} "
                      f"(seed {SEED}), OU solenoidal forcing on 1<=|n|<=2, energy reset every "
-                     f"step, CFL {args.courant}"),
+                     f"step, CFL {args.courant}"
+                     + (", exact Riemann solver flux" if getattr(args, "flux", "hllc") == "exact" else "")),
+        "flux": getattr(args, "flux", "hllc"),
         "cells": n ** 3,
         "dof_per_cell_per_var": N,
         "precision": precision,
@@ -235,6 +239,7 @@ def run_ours(args):
     n = (args.n,) * 3
     k = args.order - 1
     s = dgm.Solver(n, args.order, GAMMA, forcing=True)
+    s.set_flux(dgm.DG_FLUX_EXACT if args.flux == "exact" else dgm.DG_FLUX_HLLC)
     N, nc = s.N, s.ncells
     fn = syn.solenoidal_velocity(seed=SEED, mach=MACH, gamma=GAMMA)
     s.project_fn(fn)
@@ -343,7 +348,8 @@ def run_ours(args):
         kst = results[prec_name]["ktimes"]
         nvol, msvol = kst["volume"]
         per_launch_s = msvol / nvol * 1e-3
-        flops = rl.volume_flops(k, True) * nc
+        sumfact = k >= 2 and not (tsize == 4 and k <= 2)
+        flops = (rl.volume_sf_flops(k, True) if sumfact else rl.volume_flops(k, True)) * nc
         byts = rl.volume_bytes(k, tsize, True) * nc
         t_alu = flops / (fp64_peak if tsize == 8 else fp32_peak)
         t_hbm = byts / (hbm * 1e9) if hbm else 0.0
@@ -356,7 +362,7 @@ def run_ours(args):
             e = roofline_entry("hbm", byts / per_launch_s / 1e9, hbm, "GB/s", "hbm")
             e["peak_source"] = "measured (MEASURED_PEAKS.json hbm_gbs)"
         kname = (f"volume_f32_kernel<{k}, 1, 1>" if (tsize == 4 and k <= 2)
-                 else f"volume_kernel<{k}, {'double' if tsize == 8 else 'float'}, 1, 1>")
+                 else f"volume_{'sf_' if sumfact else ''}kernel<{k}, {'double' if tsize == 8 else 'float'}, 1, 1>")
         e["kernel"] = kname + " (stage, forcing)"
         tr = ncu_traffic().get(kname)
         if tr:

@@ -51,7 +51,7 @@ extern "C" {
 #define DG_ERR_CUDA -3         /* a CUDA runtime call failed */
 #define DG_ERR_NONFINITE -4    /* NaN/Inf found in the state */
 #define DG_ERR_POSITIVITY -5   /* a cell mean density or pressure below eps */
-#define DG_ERR_NEWTON -6       /* limiter Newton iteration did not converge */
+#define DG_ERR_NEWTON -6       /* a Newton iteration (limiter or exact flux) did not converge */
 #define DG_ERR_TOO_LARGE -7    /* problem exceeds dg_rhs_noalloc's fixed scratch */
 
 #define DG_PREC_FP64 0   /* every step in FP64 */
@@ -146,6 +146,18 @@ int dg_cfl_dt(dg_ctx* ctx, double courant, double* dt_out);
 
 /* DG_PREC_FP64 or DG_PREC_MIXED. */
 int dg_set_precision(dg_ctx* ctx, int mode);
+
+/* Numerical flux of the surface integral (Sect. 2.3, Eq.
+ * dg:eqn:surface_int, which allows an exact or an approximate HLLC Riemann
+ * solver): DG_FLUX_HLLC (default; Einfeldt wave speeds) or DG_FLUX_EXACT
+ * (Godunov flux of the exact Riemann solution, star pressure by Newton's
+ * method, at most 50 iterations; a face point whose FP64 iteration does not
+ * converge makes the next synchronising call return DG_ERR_NEWTON). Any
+ * other value: DG_ERR_ARG. Applies to dg_rhs, dg_step and the indicator
+ * capture from the next call on. */
+#define DG_FLUX_HLLC 0
+#define DG_FLUX_EXACT 1
+int dg_set_flux(dg_ctx* ctx, int flux);
 
 /* Positivity floors for density and pressure (Sect. 2.5 "minimum target
  * density"), both > 0. */

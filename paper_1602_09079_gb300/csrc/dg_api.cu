@@ -170,6 +170,12 @@ void build_tables(double* t) {
     t[TB::FEND + e] = pt(e, -1.0);
     t[TB::FEND + (K + 1) + e] = pt(e, 1.0);
   }
+  for (int u = 0; u <= K; ++u)
+    for (int a = 0; a < Q; ++a) {
+      t[TB::P1 + u * Q + a] = pt(u, g[a]);
+      t[TB::P1W + u * Q + a] = pt(u, g[a]) * gw[a];
+      t[TB::D1W + u * Q + a] = dpt(u, g[a]) * gw[a];
+    }
   for (int a = 0; a < Q; ++a) {
     t[TB::GX + a] = g[a];
     t[TB::GW + a] = gw[a];
@@ -339,6 +345,7 @@ struct dg_ctx {
   std::vector<cudaEvent_t> pool;
   // settings
   int prec = DG_PREC_FP64;
+  int flux = DG_FLUX_HLLC;
   bool limited = false;
   int n_force = 0;
   std::vector<double> modes_host;  // 9 per mode
@@ -683,7 +690,7 @@ int dg_rhs(dg_ctx* c, const double* y_dev, double* R_dev) {
     DG_TRY(convert_shadow(c, y));
     c->shadow_valid = y == c->y;
   }
-  DG_TRY(launch(c, KC_FACE, [&] { return c->fn.face(c->prec, y, c->yf, c->fh, c->geo, c->stream); }));
+  DG_TRY(launch(c, KC_FACE, [&] { return c->fn.face(c->prec, c->flux, y, c->yf, c->fh, c->geo, c->ctrl, c->stream); }));
   DG_TRY(launch(c, KC_VOLUME, [&] {
     return c->fn.volume_rhs(c->prec, force, y, c->yf, c->fh, c->field, c->geo, R_dev, c->ctrl, c->stream);
   }));
@@ -709,7 +716,7 @@ int dg_step(dg_ctx* c, double dt) {
   const double* ys = c->y;
   for (int s = 0; s < 3; ++s) {
     double* out = s < 2 ? c->ybuf : c->y;
-    DG_TRY(launch(c, KC_FACE, [&] { return c->fn.face(c->prec, ys, yf, c->fh, c->geo, c->stream); }));
+    DG_TRY(launch(c, KC_FACE, [&] { return c->fn.face(c->prec, c->flux, ys, yf, c->fh, c->geo, c->ctrl, c->stream); }));
     DG_CUDA(cudaMemsetAsync(&c->ctrl->n_flag, 0, sizeof(unsigned), c->stream));
     DG_TRY(launch(c, KC_VOLUME, [&] {
       return c->fn.volume_stage(c->prec, force, c->fh, c->field, c->geo, ys, c->y, out, a0[s], b0[s], dt, c->list,
@@ -781,6 +788,12 @@ int dg_set_precision(dg_ctx* c, int mode) {
     DG_TRY(set_device(c));
     DG_TRY(refresh_field(c));
   }
+  return DG_OK;
+}
+
+int dg_set_flux(dg_ctx* c, int flux) {
+  if (!c || (flux != DG_FLUX_HLLC && flux != DG_FLUX_EXACT)) return DG_ERR_ARG;
+  c->flux = flux;
   return DG_OK;
 }
 
@@ -899,7 +912,7 @@ int dg_indicator_capture(dg_ctx* c, double dt, uint16_t* X_dev, int8_t* flags_de
     DG_TRY(convert_shadow(c, c->y));
     c->shadow_valid = true;
   }
-  DG_TRY(launch(c, KC_FACE, [&] { return c->fn.face(c->prec, c->y, c->yf, c->fh, c->geo, c->stream); }));
+  DG_TRY(launch(c, KC_FACE, [&] { return c->fn.face(c->prec, c->flux, c->y, c->yf, c->fh, c->geo, c->ctrl, c->stream); }));
   DG_TRY(launch(c, KC_VOLUME, [&] {
     return c->fn.volume_rhs(c->prec, force, c->y, c->yf, c->fh, c->field, c->geo, c->ybuf, c->ctrl, c->stream);
   }));
@@ -1085,7 +1098,7 @@ extern "C" int dg_rhs_noalloc(const dg_mesh* mesh, int order, double gamma, int 
     to_f32_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(y_dev, yf, n);
     DG_CUDA(cudaGetLastError());
   }
-  DG_CUDA(L.face(precision, y_dev, yf, fh, g, s));
+  DG_CUDA(L.face(precision, DG_FLUX_HLLC, y_dev, yf, fh, g, ctrl, s));
   DG_CUDA(L.volume_rhs(precision, false, y_dev, yf, fh, nullptr, g, R_dev, ctrl, s));
   return DG_OK;
 }

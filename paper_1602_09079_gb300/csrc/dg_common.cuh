@@ -10,6 +10,13 @@ namespace dg {
 // ------------------------------------------------------------- sizes
 __host__ __device__ constexpr int nmodes(int k) { return (k + 1) * (k + 2) * (k + 3) / 6; }
 __host__ __device__ constexpr int gll_m(int k) { return k <= 1 ? 2 : 3; }
+// index of the tangential pair (a, b), a + b <= k, in the order a
+// ascending, b ascending
+__host__ __device__ constexpr int pair_index(int k, int a, int b) {
+  int j = 0;
+  for (int ap = 0; ap < a; ++ap) j += k - ap + 1;
+  return j + b;
+}
 // index of mode (u, v, w) in the exchange order (total degree ascending,
 // then u descending, then v descending)
 __host__ __device__ constexpr int mode_index(int u, int v, int w) {
@@ -50,8 +57,13 @@ struct Tab {
   static constexpr int F2D = LMAX + N;
   // Pt_e(-1) and Pt_e(+1), [2][K+1]
   static constexpr int FEND = F2D + Q2 * T;
+  // 1D tables at the Gauss points for sum factorisation, [K+1][Q] each:
+  // Pt_u(x_a), Pt_u(x_a) w_a, Pt_u'(x_a) w_a
+  static constexpr int P1 = FEND + 2 * (K + 1);
+  static constexpr int P1W = P1 + (K + 1) * Q;
+  static constexpr int D1W = P1W + (K + 1) * Q;
   // 1D Gauss nodes and weights, [Q] each
-  static constexpr int GX = FEND + 2 * (K + 1);
+  static constexpr int GX = D1W + (K + 1) * Q;
   static constexpr int GW = GX + Q;
   static constexpr int SIZE = GW + Q;
 };
@@ -110,10 +122,15 @@ __device__ __forceinline__ void euler_flux(int d, const T* U, const T* v, T p, T
 // (Sect. 2.3, "approximative HLLC Riemann solver"): Einfeldt wave-speed
 // estimates from Roe averages, middle wave and star states from the
 // Rankine-Hugoniot conditions across the three waves (Toro's formulation).
+__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+
 template <typename T>
 __device__ __forceinline__ void hllc_flux(int d, const T* UL, const T* UR, T gamma, T* F) {
   const T gm1 = gamma - T(1);
-  T irL = T(1) / UL[0], irR = T(1) / UR[0];
+  // one reciprocal square root per side gives 1/rho and sqrt(rho)
+  const T rL = rsq(UL[0]), rR = rsq(UR[0]);
+  const T irL = rL * rL, irR = rR * rR;
   T vL[3] = {UL[1] * irL, UL[2] * irL, UL[3] * irL};
   T vR[3] = {UR[1] * irR, UR[2] * irR, UR[3] * irR};
   T pL = gm1 * (UL[4] - T(0.5) * UL[0] * (vL[0] * vL[0] + vL[1] * vL[1] + vL[2] * vL[2]));
@@ -128,7 +145,7 @@ __device__ __forceinline__ void hllc_flux(int d, const T* UL, const T* UR, T gam
     cL = sqrt(gamma * pL * irL);
     cR = sqrt(gamma * pR * irR);
   }
-  T sL = sqrt(UL[0]), sR = sqrt(UR[0]);
+  const T sL = UL[0] * rL, sR = UR[0] * rR;
   T iss = T(1) / (sL + sR);
   T vt[3], v2 = T(0);
 #pragma unroll
@@ -136,7 +153,7 @@ __device__ __forceinline__ void hllc_flux(int d, const T* UL, const T* UR, T gam
     vt[a] = (sL * vL[a] + sR * vR[a]) * iss;
     v2 += vt[a] * vt[a];
   }
-  T Ht = (sL * (UL[4] + pL) * irL + sR * (UR[4] + pR) * irR) * iss;
+  T Ht = (rL * (UL[4] + pL) + rR * (UR[4] + pR)) * iss;
   T c2t = gm1 * (Ht - T(0.5) * v2);
   T ct = c2t > T(0) ? sqrt(c2t) : T(0);
   T uL = vL[d], uR = vR[d];
@@ -158,18 +175,191 @@ __device__ __forceinline__ void hllc_flux(int d, const T* UL, const T* UR, T gam
   T p = left ? pL : pR;
   T S = left ? SL : SR;
   T ak = left ? aL : aR;  // rho_K (S_K - u_K)
+  T ir = left ? irL : irR;
   T uk = v[d];
   euler_flux(d, U, v, p, F);
-  T chi = ak / (S - Ss);
+  // star state: chi = rho_K (S_K - u_K) / (S_K - S*), and
+  // E* = chi (E_K / rho_K + (S* - u_K) (S* + p_K / (rho_K (S_K - u_K))))
+  const T isd = T(1) / (S - Ss);
+  T chi = ak * isd;
   T Us[5];
   Us[0] = chi;
   Us[1] = chi * v[0];
   Us[2] = chi * v[1];
   Us[3] = chi * v[2];
   Us[1 + d] = chi * Ss;
-  Us[4] = chi * (U[4] / U[0] + (Ss - uk) * (Ss + p / ak));
+  Us[4] = chi * (U[4] * ir + (Ss - uk) * Ss) + (Ss - uk) * p * isd;
 #pragma unroll
   for (int i = 0; i < 5; ++i) F[i] += S * (Us[i] - U[i]);
+}
+
+// ------------------------------------------------- exact Riemann solver
+// Godunov flux from the exact solution of the Riemann problem (the exact
+// option of Sect. 2.3 next to HLLC): the star pressure p* is the root of
+// f_L(p) + f_R(p) + u_R - u_L, where f_K is the velocity jump across the
+// wave of side K (shock branch from the Rankine-Hugoniot conditions for
+// p > p_K, rarefaction branch from the Riemann invariant for p <= p_K);
+// Newton's method from the adaptive starting value (linearised estimate for
+// close pressures, else the two-rarefaction or two-shock estimate), at most
+// kExactIters steps; the face state is the self-similar solution at x/t = 0.
+// Returns ERRB_NEWTON if the iteration did not converge (FP64) or produced a
+// non-finite pressure.
+constexpr int kExactIters = 50;
+
+template <typename T>
+struct ExactSide {
+  T rho, u, p, c;
+  T A, B;   // shock branch: sqrt(A / (p + B)) (p - p_K)
+  T crf;    // rarefaction branch: 2 c_K / (gamma - 1)
+  __device__ __forceinline__ void init(T r, T un, T pr, T gamma) {
+    // FP32 traces of a state limited in FP64 can round a pressure at the
+    // floor to zero or below: clamp it to a tiny positive value
+    if constexpr (sizeof(T) == 4) pr = fmaxf(pr, 1e-30f);
+    rho = r;
+    u = un;
+    p = pr;
+    c = sqrt(gamma * pr / r);
+    A = T(2) / ((gamma + T(1)) * r);
+    B = (gamma - T(1)) / (gamma + T(1)) * pr;
+    crf = T(2) * c / (gamma - T(1));
+  }
+  // f_K(ps) and its derivative; z = (gamma - 1) / (2 gamma)
+  __device__ __forceinline__ void jump(T ps, T z, T gamma, T& f, T& df) const {
+    if (ps > p) {
+      const T q = sqrt(A / (ps + B));
+      f = (ps - p) * q;
+      df = q * (T(1) - T(0.5) * (ps - p) / (ps + B));
+    } else {
+      const T r = pow(ps / p, z);
+      f = crf * (r - T(1));
+      df = c * r / (gamma * ps);
+    }
+  }
+};
+
+// state (rho, u, p) inside the rarefaction fan of side K at x/t = 0;
+// sgn = +1 for the left fan, -1 for the right one
+template <typename T>
+__device__ __forceinline__ void fan_at_origin(const ExactSide<T>& k, T sgn, T gamma, T* W) {
+  // positive inside the fan; the clamp only absorbs rounding at its edge
+  const T cf = fmax(T(2) / (gamma + T(1)) * (k.c + sgn * T(0.5) * (gamma - T(1)) * k.u), T(0));
+  const T ratio = cf / k.c;
+  W[0] = k.rho * pow(ratio, T(2) / (gamma - T(1)));
+  W[1] = sgn * cf;
+  W[2] = k.p * pow(ratio, T(2) * gamma / (gamma - T(1)));
+}
+
+template <typename T>
+__device__ __forceinline__ unsigned exact_flux(int d, const T* UL, const T* UR, T gamma, T* F) {
+  const T gm1 = gamma - T(1);
+  const T irL = T(1) / UL[0], irR = T(1) / UR[0];
+  const T vL[3] = {UL[1] * irL, UL[2] * irL, UL[3] * irL};
+  const T vR[3] = {UR[1] * irR, UR[2] * irR, UR[3] * irR};
+  ExactSide<T> L, R;
+  L.init(UL[0], vL[d], gm1 * (UL[4] - T(0.5) * UL[0] * (vL[0] * vL[0] + vL[1] * vL[1] + vL[2] * vL[2])), gamma);
+  R.init(UR[0], vR[d], gm1 * (UR[4] - T(0.5) * UR[0] * (vR[0] * vR[0] + vR[1] * vR[1] + vR[2] * vR[2])), gamma);
+  const T du = R.u - L.u;
+  const T z = gm1 / (T(2) * gamma);
+  T W[3];
+  bool left;  // face state on the left of the contact (tangential velocities of L)
+  unsigned err = 0;
+  if (L.crf + R.crf <= du) {
+    // the rarefactions open a vacuum between their tails
+    const T tL = L.u + L.crf, tR = R.u - R.crf;
+    if (L.u - L.c >= T(0)) {
+      W[0] = L.rho; W[1] = L.u; W[2] = L.p; left = true;
+    } else if (tL > T(0)) {
+      fan_at_origin(L, T(1), gamma, W); left = true;
+    } else if (R.u + R.c <= T(0)) {
+      W[0] = R.rho; W[1] = R.u; W[2] = R.p; left = false;
+    } else if (tR < T(0)) {
+      fan_at_origin(R, T(-1), gamma, W); left = false;
+    } else {
+      W[0] = T(0); W[1] = T(0); W[2] = T(0); left = true;
+    }
+  } else {
+    const T pmin = fmin(L.p, R.p), pmax = fmax(L.p, R.p);
+    T ps = T(0.5) * (L.p + R.p) - T(0.125) * du * (L.rho + R.rho) * (L.c + R.c);
+    ps = fmax(ps, T(0));
+    if (!(pmax <= T(2) * pmin && ps >= pmin && ps <= pmax)) {
+      if (ps < pmin) {
+        const T num = L.c + R.c - T(0.5) * gm1 * du;
+        ps = pow(num / (L.c * pow(L.p, -z) + R.c * pow(R.p, -z)), T(1) / z);
+      } else {
+        const T gL = sqrt(L.A / (ps + L.B)), gR = sqrt(R.A / (ps + R.B));
+        ps = (gL * L.p + gR * R.p - du) / (gL + gR);
+      }
+    }
+    const T tiny = sizeof(T) == 8 ? T(1e-14) * pmin : fmax(T(1e-14) * pmin, T(1e-36));
+    const T tol = sizeof(T) == 8 ? T(1e-14) : T(2e-6);
+    ps = fmax(ps, tiny);
+    bool conv = false;
+    const T rtol = sizeof(T) == 8 ? T(1e-15) : T(1e-6);
+    for (int it = 0; it < kExactIters && !conv; ++it) {
+      T fl, dfl, fr, dfr;
+      L.jump(ps, z, gamma, fl, dfl);
+      R.jump(ps, z, gamma, fr, dfr);
+      const T f = fl + fr + du;
+      // residual at the rounding level of its terms (near a vacuum the root
+      // is too ill-conditioned for the relative step to reach tol)
+      if (fabs(f) <= rtol * (fabs(fl) + fabs(fr) + fabs(du))) {
+        conv = true;
+        break;
+      }
+      const T pn = fmax(ps - f / (dfl + dfr), tiny);
+      conv = fabs(pn - ps) <= tol * pn;
+      ps = pn;
+    }
+    if (!isfinite(ps) || (sizeof(T) == 8 && !conv)) err = ERRB_NEWTON;
+    T fl, dfl, fr, dfr;
+    L.jump(ps, z, gamma, fl, dfl);
+    R.jump(ps, z, gamma, fr, dfr);
+    const T us = T(0.5) * (L.u + R.u) + T(0.5) * (fr - fl);
+    left = us >= T(0);
+    const ExactSide<T>& K = left ? L : R;
+    const T sg = left ? T(1) : T(-1);  // +1: wave moves left of the contact
+    const T ratio = ps / K.p;
+    if (ps > K.p) {
+      // shock speed from the jump conditions
+      const T S = K.u - sg * K.c * sqrt((gamma + T(1)) / (T(2) * gamma) * ratio + z);
+      if (sg * S >= T(0)) {
+        W[0] = K.rho; W[1] = K.u; W[2] = K.p;
+      } else {
+        const T g6 = gm1 / (gamma + T(1));
+        W[0] = K.rho * (ratio + g6) / (g6 * ratio + T(1)); W[1] = us; W[2] = ps;
+      }
+    } else {
+      const T head = K.u - sg * K.c, tail = us - sg * K.c * pow(ratio, z);
+      if (sg * head >= T(0)) {
+        W[0] = K.rho; W[1] = K.u; W[2] = K.p;
+      } else if (sg * tail < T(0)) {
+        W[0] = K.rho * pow(ratio, T(1) / gamma); W[1] = us; W[2] = ps;
+      } else {
+        fan_at_origin(K, sg, gamma, W);
+      }
+    }
+  }
+  const T* vt = left ? vL : vR;
+  T v[3] = {vt[0], vt[1], vt[2]};
+  v[d] = W[1];
+  const T mn = W[0] * W[1];
+  F[0] = mn;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) F[1 + a] = mn * v[a];
+  F[1 + d] += W[2];
+  F[4] = (W[2] / gm1 + T(0.5) * W[0] * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) + W[2]) * W[1];
+  return err;
+}
+
+// numerical flux selected at compile time: 0 = HLLC, 1 = exact Riemann solver
+template <int FLUX, typename T>
+__device__ __forceinline__ unsigned riemann_flux(int d, const T* UL, const T* UR, T gamma, T* F) {
+  if constexpr (FLUX == 1) {
+    return exact_flux<T>(d, UL, UR, gamma, F);
+  } else {
+    hllc_flux<T>(d, UL, UR, gamma, F);
+    return 0u;
+  }
 }
 
 // --------------------------------------------------------------- limiter

@@ -38,13 +38,21 @@ const float* tab_ptr<float>() { return h_tab32[cur_dev()]; }
 
 inline unsigned grid1(long long n, int per) { return (unsigned)((n + per - 1) / per); }
 
+// FP32 degrees 0-2: tiled register kernels; sum factorisation pays from
+// degree 2 on (fewer multiply-adds than the dense quadrature)
+constexpr bool kRegF32 = KK <= 2;
+constexpr bool kSumFact = KK >= 2;
+
 template <typename T, int MODE, bool FORCE>
 cudaError_t set_volume_smem() {
-  return cudaFuncSetAttribute(volume_kernel<KK, T, MODE, FORCE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)VolCfg<KK, T>::smem(FORCE));
+  if constexpr (kSumFact)
+    return cudaFuncSetAttribute(volume_sf_kernel<KK, T, MODE, FORCE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)VolSF<KK, T>::smem());
+  else
+    return cudaFuncSetAttribute(volume_kernel<KK, T, MODE, FORCE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)VolCfg<KK, T>::smem(FORCE));
 }
 
-constexpr bool kRegF32 = KK <= 2;
 
 template <int MODE, bool FORCE>
 cudaError_t set_f32_smem_fw() {
@@ -80,24 +88,29 @@ cudaError_t upload(const double* h64, const float* h32) {
   return r;
 }
 
-template <typename T>
-cudaError_t face_t(const double* y, void* fh, const Geo& g, cudaStream_t s) {
+template <typename T, int FLUX>
+cudaError_t face_t(const double* y, void* fh, const Geo& g, Ctrl* ctrl, cudaStream_t s) {
   dim3 grid(grid1(g.nc, 32), 3);
-  face_flux_kernel<KK, T><<<grid, dim3(32, TB::Q2), 0, s>>>(y, static_cast<T*>(fh), tab_ptr<T>(), g);
+  face_flux_kernel<KK, T, FLUX><<<grid, dim3(32, TB::Q2), 0, s>>>(y, static_cast<T*>(fh), tab_ptr<T>(), g, ctrl);
   return cudaGetLastError();
 }
 
-// FP32 tiled kernels with constant-bank tables for degrees <= 2; degree 3
-// keeps the generic shared-memory kernels.
+// FP32 path: the face kernel (constant-bank tables) reads the FP32 shadow at
+// every degree; the volume kernel is the tiled register kernel for degrees
+// <= 2 and the sum-factorised shared-memory kernel for degree 3.
 
-cudaError_t face(int prec, const double* y, const float* yf, void* fh, const Geo& g, cudaStream_t s) {
-  if constexpr (kRegF32) {
-    if (prec) {
-      face_flux_f32_kernel<KK><<<grid1(g.nc, 32), 96, 0, s>>>(yf, static_cast<float*>(fh), g);
-      return cudaGetLastError();
-    }
+template <int FLUX>
+cudaError_t face_f(int prec, const double* y, const float* yf, void* fh, const Geo& g, Ctrl* ctrl, cudaStream_t s) {
+  if (prec) {  // FP32 path: sum-factorised traces of the FP32 shadow
+    face_flux_f32_kernel<KK, FLUX><<<grid1(g.nc, 32), 96, 0, s>>>(yf, static_cast<float*>(fh), g, ctrl);
+    return cudaGetLastError();
   }
-  return prec ? face_t<float>(y, fh, g, s) : face_t<double>(y, fh, g, s);
+  return face_t<double, FLUX>(y, fh, g, ctrl, s);
+}
+
+cudaError_t face(int prec, int flux, const double* y, const float* yf, void* fh, const Geo& g, Ctrl* ctrl,
+                 cudaStream_t s) {
+  return flux == 1 ? face_f<1>(prec, y, yf, fh, g, ctrl, s) : face_f<0>(prec, y, yf, fh, g, ctrl, s);
 }
 
 template <int MODE, bool FORCE>
@@ -110,11 +123,18 @@ cudaError_t vol_f32(const float* yf, const void* fh, const void* field, const Ge
 }
 
 template <typename T, int MODE, bool FORCE>
-cudaError_t vol_t(const double* y, const void* fh, const void* field, const Geo& g, StageArgs st, double* R,
-                  Ctrl* ctrl, cudaStream_t s) {
-  using CF = VolCfg<KK, T>;
-  volume_kernel<KK, T, MODE, FORCE><<<grid1(g.nc, CF::C), kThreads, CF::smem(FORCE), s>>>(
-      y, static_cast<const T*>(fh), static_cast<const T*>(field), tab_ptr<T>(), tab_ptr<double>(), g, st, R, ctrl);
+cudaError_t vol_t(const double* y, const float* yf, const void* fh, const void* field, const Geo& g, StageArgs st,
+                  double* R, Ctrl* ctrl, cudaStream_t s) {
+  if constexpr (kSumFact) {
+    using CF = VolSF<KK, T>;
+    volume_sf_kernel<KK, T, MODE, FORCE><<<grid1(g.nc, CF::C), kThreads, CF::smem(), s>>>(
+        y, yf, static_cast<const T*>(fh), static_cast<const T*>(field), tab_ptr<T>(), tab_ptr<double>(), g, st, R,
+        ctrl);
+  } else {
+    using CF = VolCfg<KK, T>;
+    volume_kernel<KK, T, MODE, FORCE><<<grid1(g.nc, CF::C), kThreads, CF::smem(FORCE), s>>>(
+        y, static_cast<const T*>(fh), static_cast<const T*>(field), tab_ptr<T>(), tab_ptr<double>(), g, st, R, ctrl);
+  }
   return cudaGetLastError();
 }
 
@@ -127,10 +147,10 @@ cudaError_t volume_rhs(int prec, bool force, const double* y, const float* yf, c
                    : vol_f32<MODE_RHS, false>(yf, fh, field, g, st, R, ctrl, s);
   }
   if (prec)
-    return force ? vol_t<float, MODE_RHS, true>(y, fh, field, g, st, R, ctrl, s)
-                 : vol_t<float, MODE_RHS, false>(y, fh, field, g, st, R, ctrl, s);
-  return force ? vol_t<double, MODE_RHS, true>(y, fh, field, g, st, R, ctrl, s)
-               : vol_t<double, MODE_RHS, false>(y, fh, field, g, st, R, ctrl, s);
+    return force ? vol_t<float, MODE_RHS, true>(y, yf, fh, field, g, st, R, ctrl, s)
+                 : vol_t<float, MODE_RHS, false>(y, yf, fh, field, g, st, R, ctrl, s);
+  return force ? vol_t<double, MODE_RHS, true>(y, yf, fh, field, g, st, R, ctrl, s)
+               : vol_t<double, MODE_RHS, false>(y, yf, fh, field, g, st, R, ctrl, s);
 }
 
 cudaError_t volume_stage(int prec, bool force, const void* fh, const void* field, const Geo& g, const double* ys,
@@ -143,10 +163,10 @@ cudaError_t volume_stage(int prec, bool force, const void* fh, const void* field
                    : vol_f32<MODE_STAGE, false>(yf, fh, field, g, st, nullptr, ctrl, s);
   }
   if (prec)
-    return force ? vol_t<float, MODE_STAGE, true>(ys, fh, field, g, st, nullptr, ctrl, s)
-                 : vol_t<float, MODE_STAGE, false>(ys, fh, field, g, st, nullptr, ctrl, s);
-  return force ? vol_t<double, MODE_STAGE, true>(ys, fh, field, g, st, nullptr, ctrl, s)
-               : vol_t<double, MODE_STAGE, false>(ys, fh, field, g, st, nullptr, ctrl, s);
+    return force ? vol_t<float, MODE_STAGE, true>(ys, yf, fh, field, g, st, nullptr, ctrl, s)
+                 : vol_t<float, MODE_STAGE, false>(ys, yf, fh, field, g, st, nullptr, ctrl, s);
+  return force ? vol_t<double, MODE_STAGE, true>(ys, yf, fh, field, g, st, nullptr, ctrl, s)
+               : vol_t<double, MODE_STAGE, false>(ys, yf, fh, field, g, st, nullptr, ctrl, s);
 }
 
 cudaError_t limit_list(double* y, const int* list, const unsigned* count, const Geo& g, Ctrl* ctrl, int count_queued,
@@ -216,7 +236,7 @@ Launchers DG_PASTE(launchers_k, DG_K)() {
   Launchers L;
   L.k = KK;
   L.upload = upload;
-  L.f32_shadow = kRegF32;
+  L.f32_shadow = true;
   L.face = face;
   L.volume_rhs = volume_rhs;
   L.volume_stage = volume_stage;

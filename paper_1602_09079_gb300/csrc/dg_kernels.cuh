@@ -68,9 +68,9 @@ __device__ __forceinline__ long long neighbour(const Geo& g, int ix, int iy, int
 // grid: x over cell groups, y = direction d.
 // Face (d, c) joins the lower cell c - e_d (left state, its high face) and
 // cell c (right state, its low face). fh[((d*5 + i)*Q2 + p)*nc + c].
-template <int K, typename T>
+template <int K, typename T, int FLUX>
 __global__ void __launch_bounds__(512) face_flux_kernel(const double* __restrict__ y, T* __restrict__ fh,
-                                                        const T* __restrict__ tab, Geo g) {
+                                                        const T* __restrict__ tab, Geo g, Ctrl* ctrl) {
   using TB = Tab<K>;
   constexpr int N = TB::N, Q2 = TB::Q2;
   const long long nc = g.nc;
@@ -96,7 +96,8 @@ __global__ void __launch_bounds__(512) face_flux_kernel(const double* __restrict
     UR[i] = aR;
   }
   T F[5];
-  hllc_flux<T>(d, UL, UR, (T)g.gamma, F);
+  const unsigned e = riemann_flux<FLUX, T>(d, UL, UR, (T)g.gamma, F);
+  if (e) atomicOr(&ctrl->err, e);
 #pragma unroll
   for (int i = 0; i < 5; ++i) fh[((size_t)(d * 5 + i) * Q2 + p) * nc + c] = F[i];
 }
@@ -292,9 +293,9 @@ __constant__ float c_tab32[Tab<3>::SIZE];
 // the coefficients are first contracted with Pt_e(+-1) along the normal into
 // the tangential coefficients E[i][(a,b)], which then give the values at all
 // Q^2 face points through the tangential products (constant tables).
-template <int K, int D>
-__device__ __forceinline__ void face_f32_dir(const float* __restrict__ yf, float* __restrict__ fh, const Geo& g,
-                                             long long c, int ix, int iy, int iz) {
+template <int K, int D, int FLUX>
+__device__ __forceinline__ unsigned face_f32_dir(const float* __restrict__ yf, float* __restrict__ fh, const Geo& g,
+                                                 long long c, int ix, int iy, int iz) {
   using TB = Tab<K>;
   constexpr int N = TB::N, Q2 = TB::Q2, T = TB::T;
   const long long nc = g.nc;
@@ -322,6 +323,7 @@ __device__ __forceinline__ void face_f32_dir(const float* __restrict__ yf, float
         }
       }
   const float gamma = (float)g.gamma;
+  unsigned err = 0;
 #pragma unroll 1
   for (int p = 0; p < Q2; ++p) {
     float UL[5], UR[5];
@@ -338,23 +340,33 @@ __device__ __forceinline__ void face_f32_dir(const float* __restrict__ yf, float
       UR[i] = aR;
     }
     float F[5];
-    hllc_flux<float>(D, UL, UR, gamma, F);
+    err |= riemann_flux<FLUX, float>(D, UL, UR, gamma, F);
 #pragma unroll
     for (int i = 0; i < 5; ++i) fh[((size_t)(D * 5 + i) * Q2 + p) * nc + c] = F[i];
   }
+  return err;
 }
 
+// CTAs per SM the face kernel's register budget is sized for (degree 3
+// keeps 2 x 5 x 10 tangential coefficients in registers)
 template <int K>
-__global__ void __launch_bounds__(96, 6) face_flux_f32_kernel(const float* __restrict__ yf, float* __restrict__ fh,
-                                                              Geo g) {
+struct FaceF32 {
+  static constexpr int MINB = K >= 3 ? 4 : 6;
+};
+
+template <int K, int FLUX>
+__global__ void __launch_bounds__(96, FaceF32<K>::MINB) face_flux_f32_kernel(const float* __restrict__ yf, float* __restrict__ fh,
+                                                              Geo g, Ctrl* ctrl) {
   const long long c = (long long)blockIdx.x * 32 + (threadIdx.x & 31);
   if (c >= g.nc) return;
   const int d = threadIdx.x >> 5;  // warp-uniform direction
   int ix, iy, iz;
   cell_xyz(c, g, ix, iy, iz);
-  if (d == 0) face_f32_dir<K, 0>(yf, fh, g, c, ix, iy, iz);
-  else if (d == 1) face_f32_dir<K, 1>(yf, fh, g, c, ix, iy, iz);
-  else face_f32_dir<K, 2>(yf, fh, g, c, ix, iy, iz);
+  unsigned e;
+  if (d == 0) e = face_f32_dir<K, 0, FLUX>(yf, fh, g, c, ix, iy, iz);
+  else if (d == 1) e = face_f32_dir<K, 1, FLUX>(yf, fh, g, c, ix, iy, iz);
+  else e = face_f32_dir<K, 2, FLUX>(yf, fh, g, c, ix, iy, iz);
+  if (e) atomicOr(&ctrl->err, e);
 }
 
 // Volume quadrature, FP32, tiled in two phases over a tile of C cells:
@@ -632,6 +644,305 @@ __global__ void __launch_bounds__(kThreads) screen_kernel(const double* __restri
   screen[cell] = limiter_screen<K>(m, a, fin, g.gamma, g.eps_rho, g.eps_p) ? 0 : 1;
 }
 
+// ============================================== sum-factorised volume kernel
+// FP64 path (and the FP32 path of degree 3): the tensor-product structure of
+// the complete-degree basis turns each contraction over the Q^3 points into
+// three one-dimensional ones (sum factorisation), every stage a cooperative
+// pass of the block over (cell, index) items in shared memory:
+//  values   A1[u,v][c] = sum_w w_uvw P_w(c); A2[u][b,c] = sum_v A1[u,v][c] P_v(b);
+//           U[a,b,c] = sum_u A2[u][b,c] P_u(a)
+//  fluxes   G_d = F_d(U) / (4 dx_d) at every point (and S/8 for the source)
+//  project  H_d[u][b,c] = sum_a G_d X_d(u,a); J[u,v][c] = sum_b H_0 Pw + H_1 Dw;
+//           I2[u,v][c] = sum_b H_2 Pw; dw_uvw = sum_c J Pw(w,c) + I2 Dw(w,c)
+//           (X_0 = Dw, X_1 = X_2 = Pw; Pw = P w_a, Dw = P' w_a)
+//  faces    Mt[a][t2] = sum_t1 Fhat Pw(a,t1); M[a,b] = +-sum_t2 Mt Pw(b,t2)/(4 dx_d);
+//           expanded along the normal by Pt_e(-1) (low face) or Pt_e(+1) (high).
+// Multiply-adds per cell and variable at degree 2: 165 for the values, 465
+// for the projection, 55 per face (dense quadrature: 270, 810, 90).
+template <int K, typename T>
+struct VolSF {
+  static constexpr int Q = K + 1, KP = K + 1, Q2 = Q * Q, Q3 = Q * Q * Q, N = nmodes(K), TP = (K + 1) * (K + 2) / 2;
+  static constexpr int mx(int a, int b) { return a > b ? a : b; }
+  static constexpr int MT0 = 14 * TP * Q;  // offset of the face moments Mt in buffer 2
+  // buffer 1: A1, U, H, M; buffer 2: A2, fluxes, (J, I2, SI | Mt)
+  static constexpr int BUF1 = mx(mx(5 * TP * Q, 5 * Q3), mx(19 * KP * Q2, 30 * TP));
+  static constexpr int BUF2 = mx(mx(5 * KP * Q2, 19 * Q3), MT0 + 30 * KP * Q);
+  static constexpr int C = sizeof(T) == 8 ? (K >= 3 ? 4 : 8) : 8;
+  static constexpr size_t smem() {
+    return (size_t)C * (8 * (5 * N + 10) + sizeof(T) * (BUF1 + BUF2));
+  }
+};
+
+template <int K>
+__device__ __forceinline__ void pair_uv(int j, int& u, int& v) {
+  u = 0;
+  while (j > K - u) {
+    j -= K - u + 1;
+    ++u;
+  }
+  v = j;
+}
+
+// (u, v, w) of mode l in the canonical order (degree ascending, u then v
+// descending).
+__device__ __forceinline__ void mode_uvw(int l, int& u, int& v, int& w) {
+  int D = 0;
+  while (l >= nmodes(D)) ++D;
+  int r = l - (D > 0 ? nmodes(D - 1) : 0);
+  u = D;
+  while (r > D - u) {
+    r -= D - u + 1;
+    --u;
+  }
+  v = D - u - r;
+  w = D - u - v;
+}
+
+template <int K, typename T, int MODE, bool FORCE>
+__global__ void __launch_bounds__(kThreads) volume_sf_kernel(const double* __restrict__ yin,
+                                                             const float* __restrict__ yf32, const T* __restrict__ fh,
+                                                             const T* __restrict__ field, const T* __restrict__ tab,
+                                                             const double* __restrict__ tab64, Geo g, StageArgs st,
+                                                             double* __restrict__ R, Ctrl* ctrl) {
+  using TB = Tab<K>;
+  using CF = VolSF<K, T>;
+  constexpr int N = TB::N, Q = CF::Q, Q2 = CF::Q2, Q3 = CF::Q3, TP = CF::TP, C = CF::C, KP = K + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* sV = reinterpret_cast<double*>(smem_raw);  // stage output (FP64)
+  double* sM = sV + 5 * N * C;
+  double* sA = sM + 5 * C;
+  T* sW = reinterpret_cast<T*>(sV);  // stage input (T), read only by the first pass
+  T* b1 = reinterpret_cast<T*>(sA + 5 * C);
+  T* b2 = b1 + CF::BUF1 * C;
+  const long long nc = g.nc;
+  const long long c0 = (long long)blockIdx.x * C;
+  const int tid = threadIdx.x;
+  const T* P1 = tab + TB::P1;
+  const T* P1W = tab + TB::P1W;
+  const T* D1W = tab + TB::D1W;
+  // stage input: FP64 state (T = double) or its FP32 shadow (T = float)
+  const double* ysrc = (MODE == MODE_STAGE) ? st.ys : yin;
+  const float* yfsrc = (MODE == MODE_STAGE) ? st.yf : yf32;
+  for (int it = tid; it < 5 * N * C; it += kThreads) {
+    const int c = it % C, r = it / C;
+    const long long cell = c0 + c;
+    T v = r == 0 ? T(1) : T(0);
+    if (cell < nc) {
+      if constexpr (sizeof(T) == 4) v = yfsrc[(size_t)r * nc + cell];
+      else v = ysrc[(size_t)r * nc + cell];
+    }
+    sW[r * C + c] = v;
+  }
+  __syncthreads();
+  // A1[i][pair(u,v)][qc] -> b1
+  for (int it = tid; it < 5 * TP * Q * C; it += kThreads) {
+    const int c = it % C, r = it / C, qc = r % Q, j = (r / Q) % TP, i = r / (Q * TP);
+    int u, v;
+    pair_uv<K>(j, u, v);
+    T a = T(0);
+    for (int w = 0; w <= K - u - v; ++w) a += sW[(i * N + mode_index(u, v, w)) * C + c] * __ldg(P1 + w * Q + qc);
+    b1[it] = a;
+  }
+  __syncthreads();
+  // A2[i][u][qb + Q qc] -> b2
+  for (int it = tid; it < 5 * KP * Q2 * C; it += kThreads) {
+    const int c = it % C, r = it / C, bc = r % Q2, u = (r / Q2) % KP, i = r / (Q2 * KP);
+    const int qb = bc % Q, qc = bc / Q;
+    T a = T(0);
+    for (int v = 0; v <= K - u; ++v) a += b1[((i * TP + pair_index(K, u, v)) * Q + qc) * C + c] * __ldg(P1 + v * Q + qb);
+    b2[it] = a;
+  }
+  __syncthreads();
+  // U[i][qa + Q qb + Q2 qc] -> b1
+  for (int it = tid; it < 5 * Q3 * C; it += kThreads) {
+    const int c = it % C, r = it / C, q = r % Q3, i = r / Q3;
+    const int qa = q % Q, bc = q / Q;
+    T a = T(0);
+#pragma unroll
+    for (int u = 0; u <= K; ++u) a += b2[((i * KP + u) * Q2 + bc) * C + c] * __ldg(P1 + u * Q + qa);
+    b1[it] = a;
+  }
+  __syncthreads();
+  // fluxes G[d*5+i][q] = F_d / (4 dx_d), source S[i-1][q] = S / 8 -> b2
+  const T gm1 = (T)(g.gamma - 1.0);
+  for (int it = tid; it < Q3 * C; it += kThreads) {
+    const int c = it % C, q = it / C;
+    T U[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) U[i] = b1[(i * Q3 + q) * C + c];
+    const T ir = T(1) / U[0];
+    const T v[3] = {U[1] * ir, U[2] * ir, U[3] * ir};
+    const T p = gm1 * (U[4] - T(0.5) * U[0] * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]));
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      T F[5];
+      euler_flux<T>(d, U, v, p, F);
+      const T sc = (T)(0.25 * g.inv_dx[d]);
+#pragma unroll
+      for (int i = 0; i < 5; ++i) b2[((d * 5 + i) * Q3 + q) * C + c] = F[i] * sc;
+    }
+    if (FORCE) {
+      const long long cell = c0 + c < nc ? c0 + c : nc - 1;  // ragged tail: in-bounds reads
+      T a[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) a[d] = __ldg(field + ((size_t)d * Q3 + q) * nc + cell);
+      const T e8 = T(0.125);
+      b2[((15 + 0) * Q3 + q) * C + c] = U[0] * a[0] * e8;
+      b2[((15 + 1) * Q3 + q) * C + c] = U[0] * a[1] * e8;
+      b2[((15 + 2) * Q3 + q) * C + c] = U[0] * a[2] * e8;
+      b2[((15 + 3) * Q3 + q) * C + c] = (U[1] * a[0] + U[2] * a[1] + U[3] * a[2]) * e8;
+    }
+  }
+  __syncthreads();
+  // H[comp][u][qb + Q qc] = sum_a G[comp][qa,qb,qc] X(u,qa) -> b1
+  constexpr int NCP = FORCE ? 19 : 15;
+  for (int it = tid; it < NCP * KP * Q2 * C; it += kThreads) {
+    const int c = it % C, r = it / C, bc = r % Q2, u = (r / Q2) % KP, comp = r / (Q2 * KP);
+    const T* X = (comp < 5) ? D1W : P1W;
+    T a = T(0);
+#pragma unroll
+    for (int qa = 0; qa < Q; ++qa) a += b2[(comp * Q3 + qa + Q * bc) * C + c] * __ldg(X + u * Q + qa);
+    b1[it] = a;
+  }
+  __syncthreads();
+  // rows 0..4: J_i = sum_b H_{0,i} Pw + H_{1,i} Dw; rows 5..9: I2_i = sum_b H_{2,i} Pw;
+  // rows 10..13: SI = sum_b SH Pw -> b2[row][pair][qc]. Face moments
+  // Mt[d*2+side][i][a][t2] = sum_t1 Fhat Pw(a, t1) -> b2 + MT0
+  constexpr int NR = FORCE ? 14 : 10;
+  constexpr int NJ = NR * TP * Q * C;
+  for (int it = tid; it < NJ + 30 * Q * C; it += kThreads) {
+    if (it < NJ) {
+      const int c = it % C, r = it / C, qc = r % Q, j = (r / Q) % TP, row = r / (Q * TP);
+      int u, v;
+      pair_uv<K>(j, u, v);
+      T a = T(0);
+      if (row < 5) {
+        const T* h0 = b1 + ((row * KP + u) * Q2) * C;
+        const T* h1 = b1 + (((5 + row) * KP + u) * Q2) * C;
+#pragma unroll
+        for (int qb = 0; qb < Q; ++qb)
+          a += h0[(qb + Q * qc) * C + c] * __ldg(P1W + v * Q + qb) + h1[(qb + Q * qc) * C + c] * __ldg(D1W + v * Q + qb);
+      } else {
+        const int comp = row < 10 ? 10 + (row - 5) : 15 + (row - 10);
+        const T* h = b1 + ((comp * KP + u) * Q2) * C;
+#pragma unroll
+        for (int qb = 0; qb < Q; ++qb) a += h[(qb + Q * qc) * C + c] * __ldg(P1W + v * Q + qb);
+      }
+      b2[it] = a;
+    } else {
+      const int jt = it - NJ;
+      const int c = jt % C, r = jt / C, t2 = r % Q, i = (r / Q) % 5, ds = r / (5 * Q);
+      const int d = ds >> 1, side = ds & 1;
+      const long long cell = c0 + c;
+      T m[KP];
+#pragma unroll
+      for (int a = 0; a <= K; ++a) m[a] = T(0);
+      if (cell < nc) {
+        long long fc = cell;  // low face: this cell's; high face: the upper cell's
+        if (side) {
+          int ix, iy, iz;
+          cell_xyz(cell, g, ix, iy, iz);
+          fc = neighbour(g, ix, iy, iz, d, +1);
+        }
+        const T* fp = fh + ((size_t)(d * 5 + i) * Q2 + Q * t2) * nc + fc;
+#pragma unroll
+        for (int t1 = 0; t1 < Q; ++t1) {
+          const T f = __ldg(fp + (size_t)t1 * nc);
+#pragma unroll
+          for (int a = 0; a <= K; ++a) m[a] += f * __ldg(P1W + a * Q + t1);
+        }
+      }
+#pragma unroll
+      for (int a = 0; a <= K; ++a) b2[CF::MT0 * C + (((ds * 5 + i) * KP + a) * Q + t2) * C + c] = m[a];
+    }
+  }
+  __syncthreads();
+  // M[d*2+side][i][pair(a,b)] = +-(1/(4 dx_d)) sum_t2 Mt[a][t2] Pw(b, t2) -> b1
+  for (int it = tid; it < 30 * TP * C; it += kThreads) {
+    const int c = it % C, r = it / C, j = r % TP, i = (r / TP) % 5, ds = r / (5 * TP);
+    const int d = ds >> 1, side = ds & 1;
+    int a, b;
+    pair_uv<K>(j, a, b);
+    const T* mt = b2 + CF::MT0 * C + (((ds * 5 + i) * KP + a) * Q) * C + c;
+    T m = T(0);
+#pragma unroll
+    for (int t2 = 0; t2 < Q; ++t2) m += mt[t2 * C] * __ldg(P1W + b * Q + t2);
+    const T sc = (T)(0.25 * g.inv_dx[d]);
+    b1[it] = side == 0 ? m * sc : -(m * sc);
+  }
+  __syncthreads();
+  // dw/dt per (cell, variable, mode): volume + source + six faces
+  for (int it = tid; it < 5 * N * C; it += kThreads) {
+    const int c = it % C, r = it / C, l = r % N, i = r / N;
+    const long long cell = c0 + c;
+    int u, v, w;
+    mode_uvw(l, u, v, w);
+    const int j = pair_index(K, u, v);
+    const T* jr = b2 + ((i * TP + j) * Q) * C + c;
+    const T* ir2 = b2 + (((5 + i) * TP + j) * Q) * C + c;
+    T a = T(0);
+#pragma unroll
+    for (int qc = 0; qc < Q; ++qc) a += jr[qc * C] * __ldg(P1W + w * Q + qc) + ir2[qc * C] * __ldg(D1W + w * Q + qc);
+    if (FORCE && i > 0) {
+      const T* sr = b2 + (((10 + i - 1) * TP + j) * Q) * C + c;
+#pragma unroll
+      for (int qc = 0; qc < Q; ++qc) a += sr[qc * C] * __ldg(P1W + w * Q + qc);
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const int e = d == 0 ? u : (d == 1 ? v : w);
+      const int pa = d == 0 ? v : u, pb = d == 2 ? v : w;
+      const int jf = pair_index(K, pa, pb);
+#pragma unroll
+      for (int side = 0; side < 2; ++side)
+        a += b1[(((d * 2 + side) * 5 + i) * TP + jf) * C + c] * __ldg(tab + TB::FEND + side * KP + e);
+    }
+    if (cell < nc) {
+      const size_t at = (size_t)r * nc + cell;
+      if (MODE == MODE_RHS) {
+        R[at] = -(double)a;
+      } else {
+        const double vv = st.a0 * st.y0[at] + st.b0 * (st.ys[at] + st.dt * (double)a);
+        st.out[at] = vv;
+        if constexpr (sizeof(T) == 4) st.yf[at] = (float)vv;
+        sV[r * C + c] = vv;
+      }
+    }
+  }
+  if (MODE == MODE_RHS) return;
+  __syncthreads();
+  // limiter screen of the next stage's input (FP64); cells that fail it are
+  // queued for the full limiter
+  for (int it = tid; it < 5 * C; it += kThreads) {
+    const int c = it % C, i = it / C;
+    if (c0 + c >= nc) continue;
+    const double* row = sV + (i * N) * C + c;
+    double sa = 0.0;
+    bool fin = isfinite(row[0]);
+    for (int l = 1; l < N; ++l) {
+      sa += fabs(row[l * C]) * __ldg(tab64 + TB::LMAX + l);
+      fin &= isfinite(row[l * C]);
+    }
+    sM[it] = fin ? row[0] : __longlong_as_double(0x7ff8000000000000LL);
+    sA[it] = sa;
+  }
+  __syncthreads();
+  if (tid < C && c0 + tid < nc) {
+    double m[5], a[5];
+    bool fin = true;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      m[i] = sM[i * C + tid];
+      a[i] = sA[i * C + tid];
+      fin &= isfinite(m[i]);
+    }
+    if (!limiter_screen<K>(m, a, fin, g.gamma, g.eps_rho, g.eps_p)) {
+      const unsigned slot = atomicAdd(&ctrl->n_flag, 1u);
+      st.list[slot] = (int)(c0 + tid);
+    }
+  }
+}
+
 // ------------------------------------------------------ standalone limiter
 template <int K>
 __global__ void __launch_bounds__(kThreads) limit_kernel(double* __restrict__ y, int8_t* __restrict__ flags,
@@ -672,13 +983,16 @@ __global__ void __launch_bounds__(kThreads) cfl_kernel(const double* __restrict_
     const double r = y[c];
     const double m1 = y[(size_t)N * nc + c], m2 = y[(size_t)2 * N * nc + c], m3 = y[(size_t)3 * N * nc + c];
     const double E = y[(size_t)4 * N * nc + c];
-    const double pr = (g.gamma - 1.0) * (E - 0.5 * (m1 * m1 + m2 * m2 + m3 * m3) / r);
+    // one division and one square root per cell (the FP64 pipe is the bound)
+    const double ir = 1.0 / r;
+    const double pr = (g.gamma - 1.0) * (E - 0.5 * (m1 * m1 + m2 * m2 + m3 * m3) * ir);
     if (!(r > 0.0) || !(pr > 0.0)) {
       e |= (isfinite(r) && isfinite(pr)) ? ERRB_POSITIVITY : ERRB_NONFINITE;
       continue;
     }
-    const double cs = sqrt(g.gamma * pr / r);
-    const double s = (fabs(m1 / r) + cs) / g.dx[0] + (fabs(m2 / r) + cs) / g.dx[1] + (fabs(m3 / r) + cs) / g.dx[2];
+    const double cs = sqrt(g.gamma * pr * ir);
+    const double s = (fabs(m1) * ir + cs) * g.inv_dx[0] + (fabs(m2) * ir + cs) * g.inv_dx[1] +
+                     (fabs(m3) * ir + cs) * g.inv_dx[2];
     smax = fmax(smax, s);
   }
 #pragma unroll
@@ -721,6 +1035,8 @@ __global__ void __launch_bounds__(kThreads) energy_reset_kernel(double* __restri
   __shared__ double sEn[N * C];   // new energy modes
   __shared__ double sM[5 * C];    // means (old energy mean in row 4)
   __shared__ double s_red[kThreads / 32];
+  __shared__ double sA[5 * C];    // sum_l |w_il| max_S |phi_l| of the reset state
+  __shared__ int sFin[5 * C];
   const long long nc = g.nc;
   const long long c0 = (long long)blockIdx.x * C;
   const int tid = threadIdx.x;
@@ -737,6 +1053,7 @@ __global__ void __launch_bounds__(kThreads) energy_reset_kernel(double* __restri
   }
   __syncthreads();
   const T gm1 = (T)(g.gamma - 1.0);
+  const bool two_thirds = fabs(g.gamma - 1.0 - 2.0 / 3.0) < 1e-15;
   const T tc2g = (T)c2g, tir0 = (T)inv_rho0;
   for (int it = tid; it < Q3 * C; it += kThreads) {
     const int c = it % C, q = it / C;
@@ -749,7 +1066,16 @@ __global__ void __launch_bounds__(kThreads) energy_reset_kernel(double* __restri
       for (int l = 0; l < N; ++l) a += sW[(i * N + l) * C + c] * __ldg(ph + l);
       U[i] = a;
     }
-    const T eps = tc2g * pow(U[0] * tir0, gm1);
+    // gamma = 5/3 (gamma - 1 within 1e-15 of 2/3): x^(2/3) as cbrt(x)^2
+    const T x = U[0] * tir0;
+    T xg;
+    if (two_thirds) {
+      const T cx = cbrt(x);
+      xg = cx * cx;
+    } else {
+      xg = pow(x, gm1);
+    }
+    const T eps = tc2g * xg;
     sE[q * C + c] = T(0.5) * (U[1] * U[1] + U[2] * U[2] + U[3] * U[3]) / U[0] + U[0] * eps;
   }
   __syncthreads();
@@ -760,6 +1086,24 @@ __global__ void __launch_bounds__(kThreads) energy_reset_kernel(double* __restri
     sEn[l * C + c] = (double)acc;
   }
   __syncthreads();
+  // limiter screen sums of the reset state (density and momentum unchanged),
+  // one (cell, variable) per thread, from the FP64 coefficients
+  for (int it = tid; it < 5 * C; it += kThreads) {
+    const int c = it % C, i = it / C;
+    const long long cell = c0 + c;
+    double sa = 0.0;
+    bool fin = true;
+    if (cell < nc) {
+      for (int l = 1; l < N; ++l) {
+        const double v = i < 4 ? __ldg(y + (size_t)(i * N + l) * nc + cell) : sEn[l * C + c];
+        sa += fabs(v) * __ldg(tab64 + TB::LMAX + l);
+        fin &= isfinite(v);
+      }
+    }
+    sA[it] = sa;
+    sFin[it] = fin;
+  }
+  __syncthreads();
   double diss = 0.0;
   if (tid < C && c0 + tid < nc) {
     const int c = tid;
@@ -767,25 +1111,13 @@ __global__ void __launch_bounds__(kThreads) energy_reset_kernel(double* __restri
     const double r = sM[c], m1 = sM[C + c], m2 = sM[2 * C + c], m3 = sM[3 * C + c];
     const double kin = 0.5 * (m1 * m1 + m2 * m2 + m3 * m3) / r;
     diss = (sM[4 * C + c] - kin) - (sEn[c] - kin);
-    // limiter screen on the reset state (density and momentum unchanged)
     double m[5] = {r, m1, m2, m3, sEn[c]}, a[5];
-    bool fin = true;
+    bool fin = isfinite(sEn[c]);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      double sa = 0.0;
-      for (int l = 1; l < N; ++l) {
-        const double v = (double)sW[(i * N + l) * C + c];
-        sa += fabs(y[(size_t)(i * N + l) * nc + cell]) * __ldg(tab64 + TB::LMAX + l);
-        fin &= isfinite(v);
-      }
-      a[i] = sa;
+    for (int i = 0; i < 5; ++i) {
+      a[i] = sA[i * C + c];
+      fin &= sFin[i * C + c] != 0;
     }
-    double sa = 0.0;
-    for (int l = 1; l < N; ++l) {
-      sa += fabs(sEn[l * C + c]) * __ldg(tab64 + TB::LMAX + l);
-      fin &= isfinite(sEn[l * C + c]);
-    }
-    a[4] = sa;
     if (!limiter_screen<K>(m, a, fin, g.gamma, g.eps_rho, g.eps_p)) {
       const unsigned slot = atomicAdd(&ctrl->n_flag, 1u);
       list[slot] = (int)cell;

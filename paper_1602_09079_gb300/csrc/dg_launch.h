@@ -17,8 +17,11 @@ struct Launchers {
   // true when the FP32 path reads an FP32 shadow of the state (yf) instead
   // of the FP64 state
   bool f32_shadow;
-  // one HLLC flux per face point; fh holds T = double (prec 0) or float (prec 1)
-  cudaError_t (*face)(int prec, const double* y, const float* yf, void* fh, const Geo& g, cudaStream_t s);
+  // one numerical flux per face point (flux 0: HLLC, 1: exact Riemann
+  // solver; a failed exact iteration sets ERRB_NEWTON in ctrl->err); fh
+  // holds T = double (prec 0) or float (prec 1)
+  cudaError_t (*face)(int prec, int flux, const double* y, const float* yf, void* fh, const Geo& g, Ctrl* ctrl,
+                      cudaStream_t s);
   // R(y) written in FP64, state layout
   cudaError_t (*volume_rhs)(int prec, bool force, const double* y, const float* yf, const void* fh,
                             const void* field, const Geo& g, double* R, Ctrl* ctrl, cudaStream_t s);

@@ -6,7 +6,14 @@ Q3 = Q^3; FMA = 2 flops; sqrt and division count as one flop each):
 face_flux_kernel (3 faces per cell, Q2 points each)
     traces of both sides  2 x 5 x N FMA           -> 20 N
     HLLC flux                                      -> HLLC_FLOPS
-volume_kernel
+volume_sf_kernel (sum factorisation; T = (k+1)(k+2)/2, KP = k+1)
+    point values          5 (Q N + Q2 T + Q3 KP) FMA
+    Euler fluxes, scaling Q3 x 46;   source  Q3 x 12 (forcing only)
+    gradient projection   15 KP Q3 + 5 T Q (2Q + Q) + 5 N 2Q FMA
+    source projection     4 (KP Q3 + T Q2 + N Q) FMA (forcing only)
+    face projection       30 (Q2 KP + T Q) FMA + 30 T + 5 N x 6 FMA
+    stage combination     5 N x 5;  limiter screen ~ 10 N + 30 (RK stage only)
+volume_kernel (dense quadrature; the FP32 tiled kernel follows the same counts)
     point values          Q3 x 5 N FMA            -> 10 N Q3
     Euler fluxes, scaling Q3 x 46                  (1 div, velocity,
                                                     pressure, 3 fluxes, 1/dx)
@@ -24,7 +31,7 @@ Algorithmic HBM bytes (unique data each launch must touch):
 """
 from __future__ import annotations
 
-HLLC_FLOPS = 116
+HLLC_FLOPS = 120
 
 
 def _dims(k):
@@ -43,6 +50,20 @@ def volume_flops(k, forcing, stage=True):
     f = 10 * N * Q3 + 46 * Q3 + 30 * Q3 * N + 15 * Q2 * (2 + 4 * N)
     if forcing:
         f += 8 * Q3 + 8 * Q3 * N
+    if stage:
+        f += 25 * N + 10 * N + 30
+    return f
+
+
+def volume_sf_flops(k, forcing, stage=True):
+    N, Q, Q2, Q3 = _dims(k)
+    T, KP = (k + 1) * (k + 2) // 2, k + 1
+    fma = 5 * (Q * N + Q2 * T + Q3 * KP)
+    fma += 15 * KP * Q3 + 5 * T * Q * 3 * Q + 5 * N * 2 * Q
+    fma += 30 * (Q2 * KP + T * Q) + 5 * N * 6
+    f = 2 * fma + 46 * Q3 + 30 * T
+    if forcing:
+        f += 12 * Q3 + 2 * 4 * (KP * Q3 + T * Q2 + N * Q)
     if stage:
         f += 25 * N + 10 * N + 30
     return f
