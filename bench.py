@@ -362,7 +362,8 @@ def run_ours(args):
             e = roofline_entry("hbm", byts / per_launch_s / 1e9, hbm, "GB/s", "hbm")
             e["peak_source"] = "measured (MEASURED_PEAKS.json hbm_gbs)"
         kname = (f"volume_f32_kernel<{k}, 1, 1>" if (tsize == 4 and k <= 2)
-                 else f"volume_{'sf_' if sumfact else ''}kernel<{k}, {'double' if tsize == 8 else 'float'}, 1, 1>")
+                 else f"volume_{('sfb_' if tsize == 4 else 'sf_') if sumfact else ''}kernel<{k}, "
+                 f"{'double' if tsize == 8 else 'float'}, 1, 1>")
         e["kernel"] = kname + " (stage, forcing)"
         tr = ncu_traffic().get(kname)
         if tr:

@@ -26,6 +26,21 @@ __host__ __device__ constexpr int mode_index(int u, int v, int w) {
   return idx + (D - u - v);
 }
 
+// (u, v, w) of mode l in the canonical order (degree ascending, u then v
+// descending).
+__device__ __forceinline__ void mode_uvw(int l, int& u, int& v, int& w) {
+  int D = 0;
+  while (l >= nmodes(D)) ++D;
+  int r = l - (D > 0 ? nmodes(D - 1) : 0);
+  u = D;
+  while (r > D - u) {
+    r -= D - u + 1;
+    --u;
+  }
+  v = D - u - r;
+  w = D - u - v;
+}
+
 // Per-degree basis/quadrature tables (Sect. 2.2-2.5), all values at the
 // method's point sets, offsets in elements. Weights are folded in so the
 // kernels only multiply and add.

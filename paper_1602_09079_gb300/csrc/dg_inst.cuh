@@ -45,8 +45,11 @@ constexpr bool kSumFact = KK >= 2;
 
 template <typename T, int MODE, bool FORCE>
 cudaError_t set_volume_smem() {
-  if constexpr (kSumFact)
+  if constexpr (kSumFact && sizeof(T) == 8)
     return cudaFuncSetAttribute(volume_sf_kernel<KK, T, MODE, FORCE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)VolSF<KK, T>::smem());
+  else if constexpr (kSumFact)
+    return cudaFuncSetAttribute(volume_sfb_kernel<KK, T, MODE, FORCE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)VolSF<KK, T>::smem());
   else
     return cudaFuncSetAttribute(volume_kernel<KK, T, MODE, FORCE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -66,6 +69,26 @@ cudaError_t upload(const double* h64, const float* h32) {
   e = cudaMemcpyToSymbol(g_tab32, h32, sizeof(float) * TB::SIZE);
   if (e != cudaSuccess) return e;
   if ((e = cudaMemcpyToSymbol(c_tab32, h32, sizeof(float) * TB::SIZE)) != cudaSuccess) return e;
+  {
+    constexpr int KQ = (KK + 1) * (KK + 1), NSF = 3 * KQ + 2 * (KK + 1);
+    double f64[3 * 16 + 8];
+    float f32[3 * 16 + 8];
+    for (int i = 0; i < KQ; ++i) {
+      f64[i] = h64[TB::P1 + i];
+      f64[KQ + i] = h64[TB::P1W + i];
+      f64[2 * KQ + i] = h64[TB::D1W + i];
+    }
+    for (int i = 0; i < 2 * (KK + 1); ++i) f64[3 * KQ + i] = h64[TB::FEND + i];
+    for (int i = 0; i < NSF; ++i) f32[i] = (float)f64[i];
+    if ((e = cudaMemcpyToSymbol(c_sf64, f64, sizeof(double) * NSF)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(c_sf32, f32, sizeof(float) * NSF)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(face_sf64_kernel<KK, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)FaceSF64<KK>::smem())) != cudaSuccess)
+      return e;
+    if ((e = cudaFuncSetAttribute(face_sf64_kernel<KK, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)FaceSF64<KK>::smem())) != cudaSuccess)
+      return e;
+  }
   void* p = nullptr;
   const int dev = cur_dev();
   if ((e = cudaGetSymbolAddress(&p, g_tab64)) != cudaSuccess) return e;
@@ -88,10 +111,10 @@ cudaError_t upload(const double* h64, const float* h32) {
   return r;
 }
 
-template <typename T, int FLUX>
-cudaError_t face_t(const double* y, void* fh, const Geo& g, Ctrl* ctrl, cudaStream_t s) {
-  dim3 grid(grid1(g.nc, 32), 3);
-  face_flux_kernel<KK, T, FLUX><<<grid, dim3(32, TB::Q2), 0, s>>>(y, static_cast<T*>(fh), tab_ptr<T>(), g, ctrl);
+template <int FLUX>
+cudaError_t face64(const double* y, void* fh, const Geo& g, Ctrl* ctrl, cudaStream_t s) {
+  using CF = FaceSF64<KK>;
+  face_sf64_kernel<KK, FLUX><<<grid1(g.nc, 32), CF::THREADS, CF::smem(), s>>>(y, static_cast<double*>(fh), g, ctrl);
   return cudaGetLastError();
 }
 
@@ -105,7 +128,7 @@ cudaError_t face_f(int prec, const double* y, const float* yf, void* fh, const G
     face_flux_f32_kernel<KK, FLUX><<<grid1(g.nc, 32), 96, 0, s>>>(yf, static_cast<float*>(fh), g, ctrl);
     return cudaGetLastError();
   }
-  return face_t<double, FLUX>(y, fh, g, ctrl, s);
+  return face64<FLUX>(y, fh, g, ctrl, s);
 }
 
 cudaError_t face(int prec, int flux, const double* y, const float* yf, void* fh, const Geo& g, Ctrl* ctrl,
@@ -125,9 +148,14 @@ cudaError_t vol_f32(const float* yf, const void* fh, const void* field, const Ge
 template <typename T, int MODE, bool FORCE>
 cudaError_t vol_t(const double* y, const float* yf, const void* fh, const void* field, const Geo& g, StageArgs st,
                   double* R, Ctrl* ctrl, cudaStream_t s) {
-  if constexpr (kSumFact) {
+  if constexpr (kSumFact && sizeof(T) == 8) {
     using CF = VolSF<KK, T>;
     volume_sf_kernel<KK, T, MODE, FORCE><<<grid1(g.nc, CF::C), kThreads, CF::smem(), s>>>(
+        y, yf, static_cast<const T*>(fh), static_cast<const T*>(field), tab_ptr<T>(), tab_ptr<double>(), g, st, R,
+        ctrl);
+  } else if constexpr (kSumFact) {
+    using CF = VolSF<KK, T>;
+    volume_sfb_kernel<KK, T, MODE, FORCE><<<grid1(g.nc, CF::C), kThreads, CF::smem(), s>>>(
         y, yf, static_cast<const T*>(fh), static_cast<const T*>(field), tab_ptr<T>(), tab_ptr<double>(), g, st, R,
         ctrl);
   } else {

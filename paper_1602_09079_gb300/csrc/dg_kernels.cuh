@@ -6,11 +6,11 @@
 // State layout: y[(i*N + l) * nc + c], rows contiguous over cells (x-fastest),
 // so every per-row access of a warp over consecutive cells is coalesced.
 //
-// One RHS evaluation = face_flux_kernel (one HLLC flux per face point, face
-// owned by its upper cell, written once) + volume_kernel (volume quadrature,
-// flux projection onto the basis gradients, the two face fluxes of each
-// direction projected onto the face traces, and an epilogue: R, or the
-// SSP-RK3 stage combination in FP64 followed by the positivity limiter of
+// One RHS evaluation = a face kernel (one Riemann flux per face point, face
+// owned by its upper cell, written once) + a volume kernel (volume
+// quadrature, flux projection onto the basis gradients, the two face fluxes
+// of each direction projected onto the face traces, and an epilogue: R, or
+// the SSP-RK3 stage combination in FP64 followed by the limiter screen of
 // the next stage's input).
 #pragma once
 #include "dg_common.cuh"
@@ -63,44 +63,9 @@ __device__ __forceinline__ long long neighbour(const Geo& g, int ix, int iy, int
 }
 
 // ------------------------------------------------------------ face fluxes
-// block: 32 consecutive cells x the Q^2 face points (threadIdx.y), so the
-// warps of one block share the two cells' coefficients through L1;
-// grid: x over cell groups, y = direction d.
 // Face (d, c) joins the lower cell c - e_d (left state, its high face) and
-// cell c (right state, its low face). fh[((d*5 + i)*Q2 + p)*nc + c].
-template <int K, typename T, int FLUX>
-__global__ void __launch_bounds__(512) face_flux_kernel(const double* __restrict__ y, T* __restrict__ fh,
-                                                        const T* __restrict__ tab, Geo g, Ctrl* ctrl) {
-  using TB = Tab<K>;
-  constexpr int N = TB::N, Q2 = TB::Q2;
-  const long long nc = g.nc;
-  const long long c = (long long)blockIdx.x * 32 + threadIdx.x;
-  if (c >= nc) return;
-  const int p = threadIdx.y, d = blockIdx.y;
-  int ix, iy, iz;
-  cell_xyz(c, g, ix, iy, iz);
-  const long long cl = neighbour(g, ix, iy, iz, d, -1);
-  const T* phL = tab + TB::FPHI + ((d * 2 + 1) * Q2 + p) * N;
-  const T* phR = tab + TB::FPHI + ((d * 2 + 0) * Q2 + p) * N;
-  T UL[5], UR[5];
-#pragma unroll
-  for (int i = 0; i < 5; ++i) {
-    T aL = T(0), aR = T(0);
-#pragma unroll
-    for (int l = 0; l < N; ++l) {
-      const size_t row = (size_t)(i * N + l) * nc;
-      aL += (T)__ldg(y + row + cl) * __ldg(phL + l);
-      aR += (T)__ldg(y + row + c) * __ldg(phR + l);
-    }
-    UL[i] = aL;
-    UR[i] = aR;
-  }
-  T F[5];
-  const unsigned e = riemann_flux<FLUX, T>(d, UL, UR, (T)g.gamma, F);
-  if (e) atomicOr(&ctrl->err, e);
-#pragma unroll
-  for (int i = 0; i < 5; ++i) fh[((size_t)(d * 5 + i) * Q2 + p) * nc + c] = F[i];
-}
+// cell c (right state, its low face), fh[((d*5 + i)*Q2 + p)*nc + c]; the
+// kernels (face_sf64_kernel, face_flux_f32_kernel) follow the FP32 section.
 
 // Screen of the positivity limiter from a cell's FP64 means and the sums
 // sabs_i = sum_{l>=1} |w_il| max_S |phi_l| (same test and margins as
@@ -284,7 +249,20 @@ __global__ void __launch_bounds__(kThreads) volume_kernel(const double* __restri
 // constant bank and becomes an FMA operand (no load instruction).
 namespace {
 __constant__ float c_tab32[Tab<3>::SIZE];
+// 1D tables of the sum-factorised kernels for this translation unit's
+// degree (KQ = (k+1)^2): Pt_u(x_a) at [u*Q + a], Pt_u(x_a) w_a at KQ + [u*Q + a],
+// Pt_u'(x_a) w_a at 2 KQ + [u*Q + a], Pt_e(-1) at 3 KQ + e, Pt_e(+1) at
+// 3 KQ + (k+1) + e. With unrolled loops every entry is a constant-bank operand.
+__constant__ float c_sf32[3 * 16 + 8];
+__constant__ double c_sf64[3 * 16 + 8];
 }
+
+template <typename T>
+__device__ __forceinline__ T sfc(int i);
+template <>
+__device__ __forceinline__ float sfc<float>(int i) { return c_sf32[i]; }
+template <>
+__device__ __forceinline__ double sfc<double>(int i) { return c_sf64[i]; }
 
 // Face fluxes, FP32 (from the FP32 shadow of the state): tiles of 32
 // consecutive cells, warp d computes the low
@@ -347,11 +325,119 @@ __device__ __forceinline__ unsigned face_f32_dir(const float* __restrict__ yf, f
   return err;
 }
 
-// CTAs per SM the face kernel's register budget is sized for (degree 3
-// keeps 2 x 5 x 10 tangential coefficients in registers)
+// Face fluxes, FP64, sum-factorised traces: tile of 32 cells, warp d = face
+// direction (the low face of each cell). Both cells' coefficients are
+// contracted along the normal with Pt_e(+-1) into the tangential
+// coefficients E[i][(a,b)]; then, per tangential Gauss row t2,
+// H[i][a] = sum_b E[i][(a,b)] Pt_b(t2) and per point U_i = sum_a H[i][a]
+// Pt_a(t1) (E and H in shared memory, one column per thread): 5 (Q T + Q^2 (k+1))
+// multiply-adds per side instead of 5 N Q^2.
+template <int K>
+struct FaceSF64 {
+  static constexpr int TP = (K + 1) * (K + 2) / 2;
+  static constexpr int THREADS = 96;
+  // per thread: E of both sides (2 x 5 x TP) and H of both sides (2 x 5 x (K+1))
+  static constexpr size_t smem() { return sizeof(double) * 2 * 5 * (TP + K + 1) * THREADS; }
+};
+
+template <int K, int D, int FLUX>
+__device__ __forceinline__ unsigned face_sf64_dir(const double* __restrict__ y, double* __restrict__ fh,
+                                                  const Geo& g, long long c, int ix, int iy, int iz, double* sE) {
+  constexpr int N = nmodes(K), Q = K + 1, KP = K + 1, Q2 = Q * Q, TP = FaceSF64<K>::TP;
+  constexpr int TH = FaceSF64<K>::THREADS, FE = 3 * KP * Q;
+  const long long nc = g.nc;
+  const long long cl = neighbour(g, ix, iy, iz, D, -1);
+  double* eL = sE + threadIdx.x;                  // [i][pair] column of this thread
+  double* eR = sE + 5 * TP * TH + threadIdx.x;
+#pragma unroll
+  for (int j = 0; j < 5 * TP; ++j) {
+    eL[j * TH] = 0.0;
+    eR[j * TH] = 0.0;
+  }
+  // one mode at a time (few live registers): its exponent along the normal
+  // selects Pt_e(+-1), the tangential pair selects the E entry
+#pragma unroll 1
+  for (int m = 0; m < N; ++m) {
+    int u, v, w;
+    mode_uvw(m, u, v, w);
+    const int e = D == 0 ? u : (D == 1 ? v : w);
+    const int j = pair_index(K, D == 0 ? v : u, D == 2 ? v : w);
+    const double pl = c_sf64[FE + KP + e];  // lower cell, xi_d = +1
+    const double pr = c_sf64[FE + e];       // own cell, xi_d = -1
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      eL[(i * TP + j) * TH] += __ldg(y + (size_t)(i * N + m) * nc + cl) * pl;
+      eR[(i * TP + j) * TH] += __ldg(y + (size_t)(i * N + m) * nc + c) * pr;
+    }
+  }
+  const double gamma = g.gamma;
+  unsigned err = 0;
+  double* hLp = sE + 2 * 5 * TP * TH + threadIdx.x;  // [i][a] column of this thread
+  double* hRp = hLp + 5 * KP * TH;
+#pragma unroll 1
+  for (int t2 = 0; t2 < Q; ++t2) {
+#pragma unroll 1
+    for (int i = 0; i < 5; ++i)
+#pragma unroll
+      for (int a = 0; a <= K; ++a) {
+        double sl = 0.0, sr = 0.0;
+#pragma unroll
+        for (int b = 0; a + b <= K; ++b) {
+          const double pb = c_sf64[b * Q + t2];
+          const int j = pair_index(K, a, b);
+          sl += eL[(i * TP + j) * TH] * pb;
+          sr += eR[(i * TP + j) * TH] * pb;
+        }
+        hLp[(i * KP + a) * TH] = sl;
+        hRp[(i * KP + a) * TH] = sr;
+      }
+#pragma unroll 1
+    for (int t1 = 0; t1 < Q; ++t1) {
+      double UL[5], UR[5];
+#pragma unroll
+      for (int i = 0; i < 5; ++i) {
+        double ul = 0.0, ur = 0.0;
+#pragma unroll
+        for (int a = 0; a <= K; ++a) {
+          const double pa = c_sf64[a * Q + t1];
+          ul += hLp[(i * KP + a) * TH] * pa;
+          ur += hRp[(i * KP + a) * TH] * pa;
+        }
+        UL[i] = ul;
+        UR[i] = ur;
+      }
+      double F[5];
+      err |= riemann_flux<FLUX, double>(D, UL, UR, gamma, F);
+      const int p = t1 + Q * t2;
+#pragma unroll
+      for (int i = 0; i < 5; ++i) fh[((size_t)(D * 5 + i) * Q2 + p) * nc + c] = F[i];
+    }
+  }
+  return err;
+}
+
+template <int K, int FLUX>
+__global__ void __launch_bounds__(FaceSF64<K>::THREADS) face_sf64_kernel(const double* __restrict__ y,
+                                                                         double* __restrict__ fh, Geo g, Ctrl* ctrl) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* sE = reinterpret_cast<double*>(smem_raw);
+  const long long c = (long long)blockIdx.x * 32 + (threadIdx.x & 31);
+  if (c >= g.nc) return;  // no block-wide barrier below
+  const int d = threadIdx.x >> 5;  // warp-uniform direction
+  int ix, iy, iz;
+  cell_xyz(c, g, ix, iy, iz);
+  unsigned e;
+  if (d == 0) e = face_sf64_dir<K, 0, FLUX>(y, fh, g, c, ix, iy, iz, sE);
+  else if (d == 1) e = face_sf64_dir<K, 1, FLUX>(y, fh, g, c, ix, iy, iz, sE);
+  else e = face_sf64_dir<K, 2, FLUX>(y, fh, g, c, ix, iy, iz, sE);
+  if (e) atomicOr(&ctrl->err, e);
+}
+
+// CTAs per SM the face kernel's register budget is sized for (measured at
+// degree 2, 128^3: 4 CTAs 0.82 ms, 6 CTAs 0.92 ms, 8 CTAs 1.06 ms)
 template <int K>
 struct FaceF32 {
-  static constexpr int MINB = K >= 3 ? 4 : 6;
+  static constexpr int MINB = 4;
 };
 
 template <int K, int FLUX>
@@ -390,7 +476,9 @@ struct VolF32 {
   static constexpr int PC = Q3 / NCH;                       // points per chunk
   static constexpr int PW = PC / NW;                        // points per phase-A warp and chunk
   static constexpr int THREADS = 5 * C;
-  static constexpr int MINB = K >= 2 ? 4 : 3;  // CTAs per SM the register budget is sized for
+  // CTAs per SM the register budget is sized for; at degree 2, 128^3, the
+  // extra occupancy outweighs the spills: 3 CTAs 5.07 ms, 4 4.02, 5 3.75, 6 3.51
+  static constexpr int MINB = K >= 2 ? 6 : 3;
   static constexpr size_t smem(bool force) {
     return sizeof(float) * (size_t)(5 * N * C + 15 * PC * C + (force ? 4 * PC * C : 0)) +
            sizeof(double) * (size_t)(10 * C);
@@ -404,22 +492,29 @@ __device__ __forceinline__ void vol_f32_points(const float* sW, float* sF, float
                                                int c, long long cell, long long nc, float gm1, const float* idx) {
   using TB = Tab<K>;
   using CF = VolF32<K>;
-  constexpr int N = TB::N, Q3 = TB::Q3, C = CF::C, PC = CF::PC;
-  float w[5 * N];
+  constexpr int N = TB::N, Q3 = TB::Q3, C = CF::C, PC = CF::PC, PW = CF::PW;
+  // values at this warp's PW points, one conserved variable at a time (only
+  // that variable's N coefficients live in registers)
+  float Up[PW][5];
 #pragma unroll
-  for (int r = 0; r < 5 * N; ++r) w[r] = sW[r * C + c];
+  for (int i = 0; i < 5; ++i) {
+    float w[N];
 #pragma unroll
-  for (int j = 0; j < CF::PW; ++j) {
-    const int ql = W * CF::PW + j;  // point within the chunk
-    const int q = CH * PC + ql;
-    float U[5];
+    for (int l = 0; l < N; ++l) w[l] = sW[(i * N + l) * C + c];
 #pragma unroll
-    for (int i = 0; i < 5; ++i) {
+    for (int j = 0; j < PW; ++j) {
+      const int q = CH * PC + W * PW + j;
       float a = 0.f;
 #pragma unroll
-      for (int l = 0; l < N; ++l) a += w[i * N + l] * c_tab32[TB::VPHI + q * N + l];
-      U[i] = a;
+      for (int l = 0; l < N; ++l) a += w[l] * c_tab32[TB::VPHI + q * N + l];
+      Up[j][i] = a;
     }
+  }
+#pragma unroll
+  for (int j = 0; j < PW; ++j) {
+    const int ql = W * PW + j;  // point within the chunk
+    const int q = CH * PC + ql;
+    const float* U = Up[j];
     const float ir = 1.f / U[0];
     const float v[3] = {U[1] * ir, U[2] * ir, U[3] * ir};
     const float p = gm1 * (U[4] - 0.5f * U[0] * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]));
@@ -683,21 +778,10 @@ __device__ __forceinline__ void pair_uv(int j, int& u, int& v) {
   v = j;
 }
 
-// (u, v, w) of mode l in the canonical order (degree ascending, u then v
-// descending).
-__device__ __forceinline__ void mode_uvw(int l, int& u, int& v, int& w) {
-  int D = 0;
-  while (l >= nmodes(D)) ++D;
-  int r = l - (D > 0 ? nmodes(D - 1) : 0);
-  u = D;
-  while (r > D - u) {
-    r -= D - u + 1;
-    --u;
-  }
-  v = D - u - r;
-  w = D - u - v;
-}
 
+// Cooperative form (FP64): one output per (cell, index) item, inner loops
+// over the exact triangular ranges, so no FP64 multiply-add is issued for an
+// absent mode (the FP64 pipe is the bound).
 template <int K, typename T, int MODE, bool FORCE>
 __global__ void __launch_bounds__(kThreads) volume_sf_kernel(const double* __restrict__ yin,
                                                              const float* __restrict__ yf32, const T* __restrict__ fh,
@@ -943,6 +1027,318 @@ __global__ void __launch_bounds__(kThreads) volume_sf_kernel(const double* __res
   }
 }
 
+// Register-blocked form (FP32): an item loads its inputs along the
+// contracted index once and produces all outputs along the new index, the
+// 1D tables as constant-bank operands. Triangular ranges become predicated
+// unrolled loops, which costs nothing where the FP32 pipe is not the bound.
+template <int K, typename T, int MODE, bool FORCE>
+__global__ void __launch_bounds__(kThreads) volume_sfb_kernel(const double* __restrict__ yin,
+                                                             const float* __restrict__ yf32, const T* __restrict__ fh,
+                                                             const T* __restrict__ field, const T* __restrict__ tab,
+                                                             const double* __restrict__ tab64, Geo g, StageArgs st,
+                                                             double* __restrict__ R, Ctrl* ctrl) {
+  using TB = Tab<K>;
+  using CF = VolSF<K, T>;
+  constexpr int N = TB::N, Q = CF::Q, Q2 = CF::Q2, Q3 = CF::Q3, TP = CF::TP, C = CF::C, KP = K + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* sV = reinterpret_cast<double*>(smem_raw);  // stage output (FP64)
+  double* sM = sV + 5 * N * C;
+  double* sA = sM + 5 * C;
+  T* sW = reinterpret_cast<T*>(sV);  // stage input (T), read only by the first pass
+  T* b1 = reinterpret_cast<T*>(sA + 5 * C);
+  T* b2 = b1 + CF::BUF1 * C;
+  const long long nc = g.nc;
+  const long long c0 = (long long)blockIdx.x * C;
+  const int tid = threadIdx.x;
+  // stage input: FP64 state (T = double) or its FP32 shadow (T = float)
+  const double* ysrc = (MODE == MODE_STAGE) ? st.ys : yin;
+  const float* yfsrc = (MODE == MODE_STAGE) ? st.yf : yf32;
+  for (int it = tid; it < 5 * N * C; it += kThreads) {
+    const int c = it % C, r = it / C;
+    const long long cell = c0 + c;
+    T v = r == 0 ? T(1) : T(0);
+    if (cell < nc) {
+      if constexpr (sizeof(T) == 4) v = yfsrc[(size_t)r * nc + cell];
+      else v = ysrc[(size_t)r * nc + cell];
+    }
+    sW[r * C + c] = v;
+  }
+  __syncthreads();
+  // Every pass below is a register-blocked 1D contraction: an item loads
+  // its inputs along the contracted index once and produces all outputs
+  // along the new index, the 1D table entries being constant-bank operands
+  // (loops unrolled over compile-time indices).
+  constexpr int OP = 0, OPW = KP * Q, ODW = 2 * KP * Q;  // P, P w, P' w in c_sf*
+  // A1[i][pair(u,v)][qc] = sum_w w_i,uvw P_w(qc) -> b1
+  for (int it = tid; it < 5 * TP * C; it += kThreads) {
+    const int c = it % C, r = it / C, j = r % TP, i = r / TP;
+    int u, v;
+    pair_uv<K>(j, u, v);
+    T acc[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) acc[q] = T(0);
+#pragma unroll
+    for (int w = 0; w <= K; ++w)
+      if (w <= K - u - v) {
+        const T x = sW[(i * N + mode_index(u, v, w)) * C + c];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) acc[q] += x * sfc<T>(OP + w * Q + q);
+      }
+#pragma unroll
+    for (int q = 0; q < Q; ++q) b1[((i * TP + j) * Q + q) * C + c] = acc[q];
+  }
+  __syncthreads();
+  // A2[i][u][qb + Q qc] = sum_v A1[i][pair(u,v)][qc] P_v(qb) -> b2
+  for (int it = tid; it < 5 * KP * Q * C; it += kThreads) {
+    const int c = it % C, r = it / C, qc = r % Q, u = (r / Q) % KP, i = r / (Q * KP);
+    T acc[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) acc[q] = T(0);
+#pragma unroll
+    for (int v = 0; v <= K; ++v)
+      if (v <= K - u) {
+        const T x = b1[((i * TP + pair_index(K, u, v)) * Q + qc) * C + c];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) acc[q] += x * sfc<T>(OP + v * Q + q);
+      }
+#pragma unroll
+    for (int q = 0; q < Q; ++q) b2[((i * KP + u) * Q2 + q + Q * qc) * C + c] = acc[q];
+  }
+  __syncthreads();
+  // U[i][qa + Q bc] = sum_u A2[i][u][bc] P_u(qa) -> b1
+  for (int it = tid; it < 5 * Q2 * C; it += kThreads) {
+    const int c = it % C, r = it / C, bc = r % Q2, i = r / Q2;
+    T acc[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) acc[q] = T(0);
+#pragma unroll
+    for (int u = 0; u <= K; ++u) {
+      const T x = b2[((i * KP + u) * Q2 + bc) * C + c];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) acc[q] += x * sfc<T>(OP + u * Q + q);
+    }
+#pragma unroll
+    for (int q = 0; q < Q; ++q) b1[(i * Q3 + q + Q * bc) * C + c] = acc[q];
+  }
+  __syncthreads();
+  // fluxes G[d*5+i][q] = F_d / (4 dx_d), source S[i-1][q] = S / 8 -> b2
+  const T gm1 = (T)(g.gamma - 1.0);
+  for (int it = tid; it < Q3 * C; it += kThreads) {
+    const int c = it % C, q = it / C;
+    T U[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) U[i] = b1[(i * Q3 + q) * C + c];
+    const T ir = T(1) / U[0];
+    const T v[3] = {U[1] * ir, U[2] * ir, U[3] * ir};
+    const T p = gm1 * (U[4] - T(0.5) * U[0] * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]));
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      T F[5];
+      euler_flux<T>(d, U, v, p, F);
+      const T sc = (T)(0.25 * g.inv_dx[d]);
+#pragma unroll
+      for (int i = 0; i < 5; ++i) b2[((d * 5 + i) * Q3 + q) * C + c] = F[i] * sc;
+    }
+    if (FORCE) {
+      const long long cell = c0 + c < nc ? c0 + c : nc - 1;  // ragged tail: in-bounds reads
+      T a[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) a[d] = __ldg(field + ((size_t)d * Q3 + q) * nc + cell);
+      const T e8 = T(0.125);
+      b2[((15 + 0) * Q3 + q) * C + c] = U[0] * a[0] * e8;
+      b2[((15 + 1) * Q3 + q) * C + c] = U[0] * a[1] * e8;
+      b2[((15 + 2) * Q3 + q) * C + c] = U[0] * a[2] * e8;
+      b2[((15 + 3) * Q3 + q) * C + c] = (U[1] * a[0] + U[2] * a[1] + U[3] * a[2]) * e8;
+    }
+  }
+  __syncthreads();
+  // H[comp][u][bc] = sum_qa G[comp][qa + Q bc] X(u, qa), X = P' w for the
+  // x-fluxes (comp < 5), P w otherwise -> b1
+  constexpr int NCP = FORCE ? 19 : 15;
+  for (int it = tid; it < NCP * Q2 * C; it += kThreads) {
+    const int c = it % C, r = it / C, bc = r % Q2, comp = r / Q2;
+    T gq[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) gq[q] = b2[(comp * Q3 + q + Q * bc) * C + c];
+    if (comp < 5) {
+#pragma unroll
+      for (int u = 0; u <= K; ++u) {
+        T a = T(0);
+#pragma unroll
+        for (int q = 0; q < Q; ++q) a += gq[q] * sfc<T>(ODW + u * Q + q);
+        b1[((comp * KP + u) * Q2 + bc) * C + c] = a;
+      }
+    } else {
+#pragma unroll
+      for (int u = 0; u <= K; ++u) {
+        T a = T(0);
+#pragma unroll
+        for (int q = 0; q < Q; ++q) a += gq[q] * sfc<T>(OPW + u * Q + q);
+        b1[((comp * KP + u) * Q2 + bc) * C + c] = a;
+      }
+    }
+  }
+  __syncthreads();
+  // rows 0..4: J_i[pair(u,v)][qc] = sum_b H_{0,i}[u][b,qc] Pw(v,b) + H_{1,i} Dw(v,b);
+  // rows 5..9: I2_i = sum_b H_{2,i} Pw; rows 10..13: SI = sum_b SH Pw -> b2.
+  // Face moments Mt[d*2+side][i][a][t2] = sum_t1 Fhat Pw(a, t1) -> b2 + MT0
+  constexpr int NR = FORCE ? 14 : 10;
+  constexpr int NJ = NR * KP * Q * C;
+  for (int it = tid; it < NJ + 30 * Q * C; it += kThreads) {
+    if (it < NJ) {
+      const int c = it % C, r = it / C, qc = r % Q, u = (r / Q) % KP, row = r / (Q * KP);
+      const int comp = row < 5 ? row : (row < 10 ? 10 + (row - 5) : 15 + (row - 10));
+      T h0[Q];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) h0[q] = b1[((comp * KP + u) * Q2 + q + Q * qc) * C + c];
+      if (row < 5) {
+        T h1[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) h1[q] = b1[(((5 + row) * KP + u) * Q2 + q + Q * qc) * C + c];
+#pragma unroll
+        for (int v = 0; v <= K; ++v)
+          if (v <= K - u) {
+            T a = T(0);
+#pragma unroll
+            for (int q = 0; q < Q; ++q) a += h0[q] * sfc<T>(OPW + v * Q + q) + h1[q] * sfc<T>(ODW + v * Q + q);
+            b2[((row * TP + pair_index(K, u, v)) * Q + qc) * C + c] = a;
+          }
+      } else {
+#pragma unroll
+        for (int v = 0; v <= K; ++v)
+          if (v <= K - u) {
+            T a = T(0);
+#pragma unroll
+            for (int q = 0; q < Q; ++q) a += h0[q] * sfc<T>(OPW + v * Q + q);
+            b2[((row * TP + pair_index(K, u, v)) * Q + qc) * C + c] = a;
+          }
+      }
+    } else {
+      const int jt = it - NJ;
+      const int c = jt % C, r = jt / C, t2 = r % Q, i = (r / Q) % 5, ds = r / (5 * Q);
+      const int d = ds >> 1, side = ds & 1;
+      const long long cell = c0 + c;
+      T m[KP];
+#pragma unroll
+      for (int a = 0; a <= K; ++a) m[a] = T(0);
+      if (cell < nc) {
+        long long fc = cell;  // low face: this cell's; high face: the upper cell's
+        if (side) {
+          int ix, iy, iz;
+          cell_xyz(cell, g, ix, iy, iz);
+          fc = neighbour(g, ix, iy, iz, d, +1);
+        }
+        const T* fp = fh + ((size_t)(d * 5 + i) * Q2 + Q * t2) * nc + fc;
+#pragma unroll
+        for (int t1 = 0; t1 < Q; ++t1) {
+          const T f = __ldg(fp + (size_t)t1 * nc);
+#pragma unroll
+          for (int a = 0; a <= K; ++a) m[a] += f * sfc<T>(OPW + a * Q + t1);
+        }
+      }
+#pragma unroll
+      for (int a = 0; a <= K; ++a) b2[CF::MT0 * C + (((ds * 5 + i) * KP + a) * Q + t2) * C + c] = m[a];
+    }
+  }
+  __syncthreads();
+  // M[d*2+side][i][pair(a,b)] = +-(1/(4 dx_d)) sum_t2 Mt[a][t2] Pw(b, t2) -> b1
+  for (int it = tid; it < 30 * KP * C; it += kThreads) {
+    const int c = it % C, r = it / C, a = r % KP, i = (r / KP) % 5, ds = r / (5 * KP);
+    const int d = ds >> 1, side = ds & 1;
+    T mt[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) mt[q] = b2[CF::MT0 * C + (((ds * 5 + i) * KP + a) * Q + q) * C + c];
+    const T sc = side == 0 ? (T)(0.25 * g.inv_dx[d]) : (T)(-0.25 * g.inv_dx[d]);
+#pragma unroll
+    for (int b = 0; b <= K; ++b)
+      if (b <= K - a) {
+        T m = T(0);
+#pragma unroll
+        for (int q = 0; q < Q; ++q) m += mt[q] * sfc<T>(OPW + b * Q + q);
+        b1[((ds * 5 + i) * TP + pair_index(K, a, b)) * C + c] = m * sc;
+      }
+  }
+  __syncthreads();
+  // dw/dt per (cell, variable, (u,v)) for all w: volume + source + six faces
+  for (int it = tid; it < 5 * TP * C; it += kThreads) {
+    const int c = it % C, r = it / C, j = r % TP, i = r / TP;
+    const long long cell = c0 + c;
+    int u, v;
+    pair_uv<K>(j, u, v);
+    T jr[Q], i2[Q], sr[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      jr[q] = b2[((i * TP + j) * Q + q) * C + c];
+      i2[q] = b2[(((5 + i) * TP + j) * Q + q) * C + c];
+      sr[q] = (FORCE && i > 0) ? b2[(((10 + i - 1) * TP + j) * Q + q) * C + c] : T(0);
+    }
+    const T* Mi = b1 + (i * TP) * C + c;  // M[ds][i][pair] at Mi[(ds*5*TP + pair) * C]
+#pragma unroll
+    for (int w = 0; w <= K; ++w)
+      if (w <= K - u - v) {
+        T a = T(0);
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+          a += jr[q] * sfc<T>(OPW + w * Q + q) + i2[q] * sfc<T>(ODW + w * Q + q);
+          if (FORCE) a += sr[q] * sfc<T>(OPW + w * Q + q);
+        }
+        // faces: along x the normal exponent is u and the tangential pair
+        // (v, w); along y v and (u, w); along z w and (u, v)
+        const int jx = pair_index(K, v, w), jy = pair_index(K, u, w);
+        a += Mi[((0 * 5) * TP + jx) * C] * __ldg(tab + TB::FEND + u) +
+             Mi[((1 * 5) * TP + jx) * C] * __ldg(tab + TB::FEND + KP + u);
+        a += Mi[((2 * 5) * TP + jy) * C] * __ldg(tab + TB::FEND + v) +
+             Mi[((3 * 5) * TP + jy) * C] * __ldg(tab + TB::FEND + KP + v);
+        a += Mi[((4 * 5) * TP + j) * C] * sfc<T>(3 * KP * Q + w) +
+             Mi[((5 * 5) * TP + j) * C] * sfc<T>(3 * KP * Q + KP + w);
+        if (cell < nc) {
+          const int l = mode_index(u, v, w);
+          const size_t at = (size_t)(i * N + l) * nc + cell;
+          if (MODE == MODE_RHS) {
+            R[at] = -(double)a;
+          } else {
+            const double vv = st.a0 * st.y0[at] + st.b0 * (st.ys[at] + st.dt * (double)a);
+            st.out[at] = vv;
+            if constexpr (sizeof(T) == 4) st.yf[at] = (float)vv;
+            sV[(i * N + l) * C + c] = vv;
+          }
+        }
+      }
+  }
+  if (MODE == MODE_RHS) return;
+  __syncthreads();
+  // limiter screen of the next stage's input (FP64); cells that fail it are
+  // queued for the full limiter
+  for (int it = tid; it < 5 * C; it += kThreads) {
+    const int c = it % C, i = it / C;
+    if (c0 + c >= nc) continue;
+    const double* row = sV + (i * N) * C + c;
+    double sa = 0.0;
+    bool fin = isfinite(row[0]);
+    for (int l = 1; l < N; ++l) {
+      sa += fabs(row[l * C]) * __ldg(tab64 + TB::LMAX + l);
+      fin &= isfinite(row[l * C]);
+    }
+    sM[it] = fin ? row[0] : __longlong_as_double(0x7ff8000000000000LL);
+    sA[it] = sa;
+  }
+  __syncthreads();
+  if (tid < C && c0 + tid < nc) {
+    double m[5], a[5];
+    bool fin = true;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      m[i] = sM[i * C + tid];
+      a[i] = sA[i * C + tid];
+      fin &= isfinite(m[i]);
+    }
+    if (!limiter_screen<K>(m, a, fin, g.gamma, g.eps_rho, g.eps_p)) {
+      const unsigned slot = atomicAdd(&ctrl->n_flag, 1u);
+      st.list[slot] = (int)(c0 + tid);
+    }
+  }
+}
+
 // ------------------------------------------------------ standalone limiter
 template <int K>
 __global__ void __launch_bounds__(kThreads) limit_kernel(double* __restrict__ y, int8_t* __restrict__ flags,
@@ -1040,12 +1436,21 @@ __global__ void __launch_bounds__(kThreads) energy_reset_kernel(double* __restri
   const long long nc = g.nc;
   const long long c0 = (long long)blockIdx.x * C;
   const int tid = threadIdx.x;
+  // FP32 path with a valid FP32 shadow: the point values come from it (no
+  // conversions on the FP64 pipe); the means stay FP64
+  const bool from_shadow = sizeof(T) == 4 && yf != nullptr;
   for (int it = tid; it < 4 * N * C; it += kThreads) {
     const int c = it % C, r = it / C;
     const long long cell = c0 + c;
-    const double v = cell < nc ? y[(size_t)r * nc + cell] : (r == 0 ? 1.0 : 0.0);
-    sW[r * C + c] = (T)v;
-    if (r % N == 0) sM[(r / N) * C + c] = v;
+    if (r % N == 0) {
+      const double v = cell < nc ? y[(size_t)r * nc + cell] : (r == 0 ? 1.0 : 0.0);
+      sW[r * C + c] = (T)v;
+      sM[(r / N) * C + c] = v;
+    } else if (from_shadow) {
+      sW[r * C + c] = cell < nc ? (T)yf[(size_t)r * nc + cell] : T(0);
+    } else {
+      sW[r * C + c] = cell < nc ? (T)y[(size_t)r * nc + cell] : T(0);
+    }
   }
   for (int c = tid; c < C; c += kThreads) {
     const long long cell = c0 + c;
@@ -1094,10 +1499,22 @@ __global__ void __launch_bounds__(kThreads) energy_reset_kernel(double* __restri
     double sa = 0.0;
     bool fin = true;
     if (cell < nc) {
-      for (int l = 1; l < N; ++l) {
-        const double v = i < 4 ? __ldg(y + (size_t)(i * N + l) * nc + cell) : sEn[l * C + c];
-        sa += fabs(v) * __ldg(tab64 + TB::LMAX + l);
-        fin &= isfinite(v);
+      if (from_shadow && i < 4) {
+        // FP32 sums of the rounded coefficients (relative error below 1e-6),
+        // widened by a relative margin of 1e-5: still a sufficient test
+        float sf = 0.f;
+        for (int l = 1; l < N; ++l) {
+          const float v = (float)sW[(i * N + l) * C + c];
+          sf += fabsf(v) * (float)__ldg(tab64 + TB::LMAX + l);
+          fin &= isfinite(v);
+        }
+        sa = (double)sf * (1.0 + 1e-5);
+      } else {
+        for (int l = 1; l < N; ++l) {
+          const double v = i < 4 ? __ldg(y + (size_t)(i * N + l) * nc + cell) : sEn[l * C + c];
+          sa += fabs(v) * __ldg(tab64 + TB::LMAX + l);
+          fin &= isfinite(v);
+        }
       }
     }
     sA[it] = sa;

@@ -45,6 +45,14 @@ def face_flops(k):
     return 3 * Q2 * (20 * N + HLLC_FLOPS)
 
 
+def face_sf_flops(k):
+    """face_sf64_kernel: per face, 2 x 5 N FMA along the normal, then per
+    side 5 (Q T + Q^2 (k+1)) FMA for the Q^2 points, and the flux."""
+    N, Q, Q2, Q3 = _dims(k)
+    T = (k + 1) * (k + 2) // 2
+    return 3 * (2 * (2 * 5 * N) + 2 * 2 * 5 * (Q * T + Q2 * (k + 1)) + Q2 * HLLC_FLOPS)
+
+
 def volume_flops(k, forcing, stage=True):
     N, Q, Q2, Q3 = _dims(k)
     f = 10 * N * Q3 + 46 * Q3 + 30 * Q3 * N + 15 * Q2 * (2 + 4 * N)
