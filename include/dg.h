@@ -291,6 +291,16 @@ int dg_rhs_noalloc(const dg_mesh* mesh, int order, double gamma, int precision, 
  * with CUDA events; takes tens of milliseconds. */
 int dg_probe_fma_peak(int fp64, double* flops_per_s);
 
+/* Self-test of the library's integer-pipe IEEE 754 conversions (binary64 ->
+ * binary32 round-to-nearest-even, binary32 -> binary64, finite test), which
+ * the FP32 path's FP64 stage epilogue uses, against the hardware conversions
+ * on n generated values (raw bit patterns, rounding ties and their
+ * neighbours, exponents at the binary32 range edges; seed selects them). No
+ * counterpart in the paper. *mismatches (host) receives the number of
+ * differing results (0 expected). Allocates 8 bytes of device memory for the
+ * duration of the call; synchronises. */
+int dg_selftest_conversions(long long n, unsigned long long seed, long long* mismatches);
+
 #ifdef __cplusplus
 }
 #endif

@@ -64,6 +64,7 @@ _SIGS = {
     "dg_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
     "dg_kernel_stats": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "dg_probe_fma_peak": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
+    "dg_selftest_conversions": (C.c_int, [C.c_longlong, C.c_ulonglong, C.POINTER(C.c_longlong)]),
     "dg_rhs_noalloc": (C.c_int, [C.POINTER(dg_mesh), C.c_int, C.c_double, C.c_int, C.c_void_p, C.c_void_p,
                                  C.c_void_p]),
     "dg_indicator_sizes": (C.c_int, [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_size_t),
@@ -299,6 +300,12 @@ def dg_limiter_counts(ctx):
     q, f = C.c_int64(0), C.c_int64(0)
     _check(load().dg_limiter_counts(ctx, C.byref(q), C.byref(f)), "dg_limiter_counts")
     return q.value, f.value
+
+
+def dg_selftest_conversions(n, seed=0):
+    v = C.c_longlong(0)
+    _check(load().dg_selftest_conversions(int(n), int(seed), C.byref(v)), "dg_selftest_conversions")
+    return v.value
 
 
 def dg_probe_fma_peak(fp64):

@@ -977,6 +977,55 @@ int dg_kernel_stats(dg_ctx* c, int64_t* launches, double* ms) {
   return st;
 }
 
+namespace {
+// splitmix64 step (Steele, Lea, Flood 2014) as a counter-based generator
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// every 8th value: a rounding tie or a neighbour of one; every 8th + 1: an
+// exponent near the edges of the binary32 range; else raw bit patterns
+__global__ void conversion_check_kernel(long long n, unsigned long long seed, unsigned long long* bad) {
+  unsigned long long nbad = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    unsigned long long b = mix64(seed ^ mix64((unsigned long long)i));
+    if (i % 8 == 0) b = (b & ~0x1fffffffull) | (0x10000000ull + (b >> 62) - 1);
+    if (i % 8 == 1) {
+      const unsigned long long e = 860 + (b >> 58) % 48 + ((b >> 57) & 1) * 260;  // 860..907 or 1120..1167
+      b = (b & 0x800fffffffffffffull) | (e << 52);
+    }
+    const double x = __longlong_as_double((long long)b);
+    const float hw = (float)x, sw = f64_to_f32(x);
+    if (!(__float_as_uint(hw) == __float_as_uint(sw) || (isnan(hw) && isnan(sw)))) ++nbad;
+    const float f = __uint_as_float((unsigned)(b >> 32));
+    const double hw2 = (double)f, sw2 = f32_to_f64(f);
+    if (!(__double_as_longlong(hw2) == __double_as_longlong(sw2) || (isnan(hw2) && isnan(sw2)))) ++nbad;
+    if (finite64(x) != (bool)isfinite(x)) ++nbad;
+  }
+  if (nbad) atomicAdd(bad, nbad);
+}
+}  // namespace
+
+int dg_selftest_conversions(long long n, unsigned long long seed, long long* mismatches) {
+  if (n < 0 || !mismatches) return DG_ERR_ARG;
+  unsigned long long* d = nullptr;
+  DG_CUDA(cudaMalloc(&d, sizeof(unsigned long long)));
+  unsigned long long h = 0;
+  cudaError_t e = cudaMemset(d, 0, sizeof(unsigned long long));
+  if (e == cudaSuccess) {
+    conversion_check_kernel<<<1216, 256>>>(n, seed, d);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof(h), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return DG_ERR_CUDA;
+  *mismatches = (long long)h;
+  return DG_OK;
+}
+
 int dg_probe_fma_peak(int fp64, double* flops_per_s) {
   if (!flops_per_s) return DG_ERR_ARG;
   int dev = 0, sms = 0;

@@ -137,6 +137,45 @@ __device__ __forceinline__ void euler_flux(int d, const T* U, const T* v, T p, T
 // (Sect. 2.3, "approximative HLLC Riemann solver"): Einfeldt wave-speed
 // estimates from Roe averages, middle wave and star states from the
 // Rankine-Hugoniot conditions across the three waves (Toro's formulation).
+// ------------------------------------------- IEEE 754 conversions
+// binary32 <-> binary64 from the format definitions (sign, biased exponent,
+// fraction) on the integer pipe, for the FP32 path's FP64 stage epilogue:
+// GB300 issues the hardware conversions on its FP64 unit, which the FP32
+// volume kernel otherwise keeps 45 % busy. Exact for every input: values
+// outside the fast range (zeros, subnormals, infinities, NaNs) take the
+// hardware conversion. dg_selftest_conversions compares both with the
+// hardware.
+
+// binary32 -> binary64: exponent rebias 127 -> 1023, fraction widened
+__device__ __forceinline__ double f32_to_f64(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned e = (u >> 23) & 0xffu;
+  if (e == 0u || e == 0xffu) return (double)x;
+  const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
+
+// binary64 -> binary32, round to nearest, ties to even: results in the
+// binary32 normal range (biased exponents 897..1150) and magnitudes below
+// 2^-150 (round to a signed zero) on the integer pipe
+__device__ __forceinline__ float f64_to_f32(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned e = (hi >> 20) & 0x7ffu;
+  if (e - 897u <= 253u) {
+    unsigned f = (hi & 0x80000000u) | ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const unsigned rem = lo & 0x1fffffffu;  // the 29 dropped fraction bits
+    f += (rem > 0x10000000u || (rem == 0x10000000u && (f & 1u))) ? 1u : 0u;
+    return __uint_as_float(f);
+  }
+  if (e < 873u) return __uint_as_float(hi & 0x80000000u);
+  return (float)x;
+}
+
+// finite test on the exponent field (integer pipe)
+__device__ __forceinline__ bool finite64(double x) {
+  return (((unsigned)__double2hiint(x) >> 20) & 0x7ffu) != 0x7ffu;
+}
+
 __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
 

@@ -649,7 +649,7 @@ __global__ void __launch_bounds__(VolF32<K>::THREADS, VolF32<K>::MINB) volume_f3
   if (MODE == MODE_RHS) {
     if (live) {
 #pragma unroll
-      for (int l = 0; l < N; ++l) R[(size_t)(i * N + l) * nc + cell] = -(double)acc[l];
+      for (int l = 0; l < N; ++l) R[(size_t)(i * N + l) * nc + cell] = -f32_to_f64(acc[l]);
     }
     return;
   }
@@ -660,11 +660,11 @@ __global__ void __launch_bounds__(VolF32<K>::THREADS, VolF32<K>::MINB) volume_f3
 #pragma unroll
     for (int l = 0; l < N; ++l) {
       const size_t a = (size_t)(i * N + l) * nc + cell;
-      const double v = st.a0 * __ldcg(st.y0 + a) + st.b0 * (__ldcg(st.ys + a) + st.dt * (double)acc[l]);
+      const double v = st.a0 * __ldcg(st.y0 + a) + st.b0 * (__ldcg(st.ys + a) + st.dt * f32_to_f64(acc[l]));
       st.out[a] = v;
-      const float vf = (float)v;
+      const float vf = f64_to_f32(v);
       st.yf[a] = vf;
-      finite &= isfinite(v);
+      finite &= finite64(v);
       if (l == 0) mean = v;
       else sabsf += fabsf(vf) * c_tab32[TB::LMAX + l];
     }
@@ -1037,6 +1037,7 @@ __global__ void __launch_bounds__(kThreads) volume_sfb_kernel(const double* __re
                                                              const T* __restrict__ field, const T* __restrict__ tab,
                                                              const double* __restrict__ tab64, Geo g, StageArgs st,
                                                              double* __restrict__ R, Ctrl* ctrl) {
+  static_assert(sizeof(T) == 4, "register-blocked form: FP32 path only");
   using TB = Tab<K>;
   using CF = VolSF<K, T>;
   constexpr int N = TB::N, Q = CF::Q, Q2 = CF::Q2, Q3 = CF::Q3, TP = CF::TP, C = CF::C, KP = K + 1;
@@ -1295,11 +1296,11 @@ __global__ void __launch_bounds__(kThreads) volume_sfb_kernel(const double* __re
           const int l = mode_index(u, v, w);
           const size_t at = (size_t)(i * N + l) * nc + cell;
           if (MODE == MODE_RHS) {
-            R[at] = -(double)a;
+            R[at] = -f32_to_f64(a);
           } else {
-            const double vv = st.a0 * st.y0[at] + st.b0 * (st.ys[at] + st.dt * (double)a);
+            const double vv = st.a0 * st.y0[at] + st.b0 * (st.ys[at] + st.dt * f32_to_f64(a));
             st.out[at] = vv;
-            if constexpr (sizeof(T) == 4) st.yf[at] = (float)vv;
+            st.yf[at] = f64_to_f32(vv);
             sV[(i * N + l) * C + c] = vv;
           }
         }
@@ -1488,7 +1489,8 @@ __global__ void __launch_bounds__(kThreads) energy_reset_kernel(double* __restri
     const int c = it % C, l = it / C;
     T acc = T(0);
     for (int q = 0; q < Q3; ++q) acc += sE[q * C + c] * __ldg(tab + TB::VPHIW + q * N + l);
-    sEn[l * C + c] = (double)acc;
+    if constexpr (sizeof(T) == 4) sEn[l * C + c] = f32_to_f64(acc);
+    else sEn[l * C + c] = acc;
   }
   __syncthreads();
   // limiter screen sums of the reset state (density and momentum unchanged),
@@ -1555,7 +1557,7 @@ __global__ void __launch_bounds__(kThreads) energy_reset_kernel(double* __restri
     const long long cell = c0 + c;
     if (cell < nc) {
       y[(size_t)(4 * N + l) * nc + cell] = sEn[l * C + c];
-      if (yf) yf[(size_t)(4 * N + l) * nc + cell] = (float)sEn[l * C + c];
+      if (yf) yf[(size_t)(4 * N + l) * nc + cell] = f64_to_f32(sEn[l * C + c]);
     }
   }
 }
