@@ -350,7 +350,12 @@ def run_ours(args):
         per_launch_s = msvol / nvol * 1e-3
         sumfact = k >= 2 and not (tsize == 4 and k <= 2)
         flops = (rl.volume_sf_flops(k, True) if sumfact else rl.volume_flops(k, True)) * nc
-        byts = rl.volume_bytes(k, tsize, True) * nc
+        # the FP32 stage kernels skip y_0 in the first stage (a0 = 0): the
+        # algorithmic bytes per launch are the average over the three stages
+        if tsize == 4:
+            byts = (rl.volume_bytes(k, tsize, True, reads_y0=False) + 2 * rl.volume_bytes(k, tsize, True)) / 3 * nc
+        else:
+            byts = rl.volume_bytes(k, tsize, True) * nc
         t_alu = flops / (fp64_peak if tsize == 8 else fp32_peak)
         t_hbm = byts / (hbm * 1e9) if hbm else 0.0
         if t_alu >= t_hbm:

@@ -1,6 +1,8 @@
 // dg_inst.cuh -- instantiates the kernels and launchers for one polynomial
 // degree DG_K (included by dg_k<K>.cu with DG_K defined).
 #pragma once
+#include <cmath>
+
 #include "dg_kernels.cuh"
 #include "dg_launch.h"
 
@@ -227,8 +229,13 @@ cudaError_t reset_t(double* y, const Geo& g, double c2g, double inv_rho0, double
                     Ctrl* ctrl, float* yf, cudaStream_t s) {
   unsigned nb = grid1(g.nc, kResetCells);
   *n_part = (int)nb;
-  energy_reset_kernel<KK, T, kResetCells><<<nb, kThreads, 0, s>>>(y, tab_ptr<T>(), tab_ptr<double>(), g, c2g, inv_rho0,
-                                                                  part, list, ctrl, yf);
+  ResetConsts<T> rc;
+  rc.c2g = (T)c2g;
+  rc.inv_rho0 = (T)inv_rho0;
+  rc.gm1 = (T)(g.gamma - 1.0);
+  rc.two_thirds = std::fabs(g.gamma - 1.0 - 2.0 / 3.0) < 1e-15 ? 1 : 0;
+  energy_reset_kernel<KK, T, kResetCells><<<nb, kThreads, 0, s>>>(y, tab_ptr<T>(), tab_ptr<double>(), g, rc, part,
+                                                                  list, ctrl, yf);
   return cudaGetLastError();
 }
 

@@ -476,9 +476,10 @@ struct VolF32 {
   static constexpr int PC = Q3 / NCH;                       // points per chunk
   static constexpr int PW = PC / NW;                        // points per phase-A warp and chunk
   static constexpr int THREADS = 5 * C;
-  // CTAs per SM the register budget is sized for; at degree 2, 128^3, the
-  // extra occupancy outweighs the spills: 3 CTAs 5.07 ms, 4 4.02, 5 3.75, 6 3.51
-  static constexpr int MINB = K >= 2 ? 6 : 3;
+  // CTAs per SM the register budget is sized for (degree 2: 56 registers,
+  // no spills; 7 CTAs also fill the shared memory). Measured at 128^3,
+  // degree 2: 5 CTAs 3.49 ms, 6 3.13, 7 3.00, 8 3.12
+  static constexpr int MINB = K >= 2 ? 7 : 3;
   static constexpr size_t smem(bool force) {
     return sizeof(float) * (size_t)(5 * N * C + 15 * PC * C + (force ? 4 * PC * C : 0)) +
            sizeof(double) * (size_t)(10 * C);
@@ -493,28 +494,21 @@ __device__ __forceinline__ void vol_f32_points(const float* sW, float* sF, float
   using TB = Tab<K>;
   using CF = VolF32<K>;
   constexpr int N = TB::N, Q3 = TB::Q3, C = CF::C, PC = CF::PC, PW = CF::PW;
-  // values at this warp's PW points, one conserved variable at a time (only
-  // that variable's N coefficients live in registers)
-  float Up[PW][5];
-#pragma unroll
-  for (int i = 0; i < 5; ++i) {
-    float w[N];
-#pragma unroll
-    for (int l = 0; l < N; ++l) w[l] = sW[(i * N + l) * C + c];
-#pragma unroll
-    for (int j = 0; j < PW; ++j) {
-      const int q = CH * PC + W * PW + j;
-      float a = 0.f;
-#pragma unroll
-      for (int l = 0; l < N; ++l) a += w[l] * c_tab32[TB::VPHI + q * N + l];
-      Up[j][i] = a;
-    }
-  }
+  // one point at a time: the coefficients are re-read from shared memory
+  // for each point, so no more than the point's five values stay live (the
+  // kernel then fits its register budget without spilling)
 #pragma unroll
   for (int j = 0; j < PW; ++j) {
     const int ql = W * PW + j;  // point within the chunk
     const int q = CH * PC + ql;
-    const float* U = Up[j];
+    float U[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      float a = 0.f;
+#pragma unroll
+      for (int l = 0; l < N; ++l) a += sW[(i * N + l) * C + c] * c_tab32[TB::VPHI + q * N + l];
+      U[i] = a;
+    }
     const float ir = 1.f / U[0];
     const float v[3] = {U[1] * ir, U[2] * ir, U[3] * ir};
     const float p = gm1 * (U[4] - 0.5f * U[0] * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]));
@@ -656,11 +650,15 @@ __global__ void __launch_bounds__(VolF32<K>::THREADS, VolF32<K>::MINB) volume_f3
   double mean = 0.0;
   float sabsf = 0.f;
   bool finite = true;
+  // first stage (a0 = 0, b0 = 1): out = y_s + dt dw/dt exactly, without
+  // reading y_0
+  const bool first = st.a0 == 0.0 && st.b0 == 1.0;
   if (live) {
 #pragma unroll
     for (int l = 0; l < N; ++l) {
       const size_t a = (size_t)(i * N + l) * nc + cell;
-      const double v = st.a0 * __ldcg(st.y0 + a) + st.b0 * (__ldcg(st.ys + a) + st.dt * f32_to_f64(acc[l]));
+      const double inc = __ldcg(st.ys + a) + st.dt * f32_to_f64(acc[l]);
+      const double v = first ? inc : st.a0 * __ldcg(st.y0 + a) + st.b0 * inc;
       st.out[a] = v;
       const float vf = f64_to_f32(v);
       st.yf[a] = vf;
@@ -1298,7 +1296,8 @@ __global__ void __launch_bounds__(kThreads) volume_sfb_kernel(const double* __re
           if (MODE == MODE_RHS) {
             R[at] = -f32_to_f64(a);
           } else {
-            const double vv = st.a0 * st.y0[at] + st.b0 * (st.ys[at] + st.dt * f32_to_f64(a));
+            const double inc = st.ys[at] + st.dt * f32_to_f64(a);
+            const double vv = (st.a0 == 0.0 && st.b0 == 1.0) ? inc : st.a0 * st.y0[at] + st.b0 * inc;
             st.out[at] = vv;
             st.yf[at] = f64_to_f32(vv);
             sV[(i * N + l) * C + c] = vv;
@@ -1419,10 +1418,18 @@ __global__ void __launch_bounds__(kThreads) cfl_kernel(const double* __restrict_
 // that then fail the limiter screen are queued (list / ctrl->n_flag) for the
 // full limiter. part[blockIdx.x] receives the block's sum of
 // (e_before - e_after), e = E - |m|^2 / (2 rho) from the means.
+// Constants of the energy reset in the kernel's arithmetic type, prepared
+// on the host (the FP32 kernel then does no per-thread FP64 set-up work).
+template <typename T>
+struct ResetConsts {
+  T c2g, inv_rho0, gm1;  // c^2/(gamma-1), 1/rho0, gamma-1
+  int two_thirds;        // gamma - 1 within 1e-15 of 2/3
+};
+
 template <int K, typename T, int C>
 __global__ void __launch_bounds__(kThreads) energy_reset_kernel(double* __restrict__ y, const T* __restrict__ tab,
-                                                                const double* __restrict__ tab64, Geo g, double c2g,
-                                                                double inv_rho0, double* __restrict__ part,
+                                                                const double* __restrict__ tab64, Geo g,
+                                                                ResetConsts<T> rc, double* __restrict__ part,
                                                                 int* __restrict__ list, Ctrl* ctrl,
                                                                 float* __restrict__ yf) {
   using TB = Tab<K>;
@@ -1431,7 +1438,7 @@ __global__ void __launch_bounds__(kThreads) energy_reset_kernel(double* __restri
   __shared__ T sE[Q3 * C];
   __shared__ double sEn[N * C];   // new energy modes
   __shared__ double sM[5 * C];    // means (old energy mean in row 4)
-  __shared__ double s_red[kThreads / 32];
+  static_assert(C == 32, "one warp's worth of cells: the dissipation sum is a warp reduction");
   __shared__ double sA[5 * C];    // sum_l |w_il| max_S |phi_l| of the reset state
   __shared__ int sFin[5 * C];
   const long long nc = g.nc;
@@ -1445,7 +1452,8 @@ __global__ void __launch_bounds__(kThreads) energy_reset_kernel(double* __restri
     const long long cell = c0 + c;
     if (r % N == 0) {
       const double v = cell < nc ? y[(size_t)r * nc + cell] : (r == 0 ? 1.0 : 0.0);
-      sW[r * C + c] = (T)v;
+      if constexpr (sizeof(T) == 4) sW[r * C + c] = f64_to_f32(v);
+      else sW[r * C + c] = v;
       sM[(r / N) * C + c] = v;
     } else if (from_shadow) {
       sW[r * C + c] = cell < nc ? (T)yf[(size_t)r * nc + cell] : T(0);
@@ -1458,9 +1466,9 @@ __global__ void __launch_bounds__(kThreads) energy_reset_kernel(double* __restri
     sM[4 * C + c] = cell < nc ? y[(size_t)(4 * N) * nc + cell] : 0.0;
   }
   __syncthreads();
-  const T gm1 = (T)(g.gamma - 1.0);
-  const bool two_thirds = fabs(g.gamma - 1.0 - 2.0 / 3.0) < 1e-15;
-  const T tc2g = (T)c2g, tir0 = (T)inv_rho0;
+  const T gm1 = rc.gm1;
+  const bool two_thirds = rc.two_thirds != 0;
+  const T tc2g = rc.c2g, tir0 = rc.inv_rho0;
   for (int it = tid; it < Q3 * C; it += kThreads) {
     const int c = it % C, q = it / C;
     const T* ph = tab + TB::VPHI + q * N;
@@ -1501,13 +1509,14 @@ __global__ void __launch_bounds__(kThreads) energy_reset_kernel(double* __restri
     double sa = 0.0;
     bool fin = true;
     if (cell < nc) {
-      if (from_shadow && i < 4) {
+      if (from_shadow) {
         // FP32 sums of the rounded coefficients (relative error below 1e-6),
         // widened by a relative margin of 1e-5: still a sufficient test
         float sf = 0.f;
+#pragma unroll
         for (int l = 1; l < N; ++l) {
-          const float v = (float)sW[(i * N + l) * C + c];
-          sf += fabsf(v) * (float)__ldg(tab64 + TB::LMAX + l);
+          const float v = i < 4 ? (float)sW[(i * N + l) * C + c] : f64_to_f32(sEn[l * C + c]);
+          sf += fabsf(v) * c_tab32[TB::LMAX + l];
           fin &= isfinite(v);
         }
         sa = (double)sf * (1.0 + 1e-5);
@@ -1542,15 +1551,12 @@ __global__ void __launch_bounds__(kThreads) energy_reset_kernel(double* __restri
       list[slot] = (int)cell;
     }
   }
-  // block sum of the dissipation (fixed order: deterministic)
+  // block sum of the dissipation: the C = 32 cells are warp 0's (fixed
+  // shuffle order: deterministic)
+  if (tid < 32) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) diss += __shfl_xor_sync(0xffffffffu, diss, o);
-  if ((tid & 31) == 0) s_red[tid >> 5] = diss;
-  __syncthreads();
-  if (tid == 0) {
-    double sum = 0.0;
-    for (int w = 0; w < kThreads / 32; ++w) sum += s_red[w];
-    part[blockIdx.x] = sum;
+    for (int o = 16; o > 0; o >>= 1) diss += __shfl_xor_sync(0xffffffffu, diss, o);
+    if (tid == 0) part[blockIdx.x] = diss;
   }
   for (int it = tid; it < N * C; it += kThreads) {
     const int c = it % C, l = it / C;
