@@ -353,7 +353,8 @@ def run_ours(args):
         # the FP32 stage kernels skip y_0 in the first stage (a0 = 0): the
         # algorithmic bytes per launch are the average over the three stages
         if tsize == 4:
-            byts = (rl.volume_bytes(k, tsize, True, reads_y0=False) + 2 * rl.volume_bytes(k, tsize, True)) / 3 * nc
+            byts = (rl.volume_bytes(k, tsize, True, reads_y0=False, shadow=True)
+                    + 2 * rl.volume_bytes(k, tsize, True, shadow=True)) / 3 * nc
         else:
             byts = rl.volume_bytes(k, tsize, True) * nc
         t_alu = flops / (fp64_peak if tsize == 8 else fp32_peak)

@@ -27,7 +27,8 @@ volume_kernel (dense quadrature; the FP32 tiled kernel follows the same counts)
 Algorithmic HBM bytes (unique data each launch must touch):
     face:   read y_s (5 N x 8) + write face fluxes (15 Q2 x sizeof(T))
     volume: read y_s, y_0 (stages 2-3), face fluxes, forcing field
-            (3 Q3 x sizeof(T)), write y_{s+1} (5 N x 8 each)
+            (3 Q3 x sizeof(T)), write y_{s+1} (5 N x 8 each); the FP32 stage
+            kernels also read and write the FP32 shadow (5 N x 4 each)
 """
 from __future__ import annotations
 
@@ -82,11 +83,15 @@ def face_bytes(k, tsize):
     return 5 * N * 8 + 15 * Q2 * tsize
 
 
-def volume_bytes(k, tsize, forcing, reads_y0=True):
+def volume_bytes(k, tsize, forcing, reads_y0=True, shadow=False):
+    """shadow: the FP32 stage kernels also read the stage input's FP32
+    shadow and write the output's (5 N x 4 bytes each way)."""
     N, Q, Q2, Q3 = _dims(k)
     b = 5 * N * 8 * (3 if reads_y0 else 2) + 15 * Q2 * tsize
     if forcing:
         b += 3 * Q3 * tsize
+    if shadow:
+        b += 2 * 5 * N * 4
     return b
 
 
