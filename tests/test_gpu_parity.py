@@ -222,6 +222,44 @@ def test_totals_and_conservation(dg):
     assert np.max(np.abs(t1 - t0) / np.abs(t0).clip(1e-3)) <= 1e-13
 
 
+def test_config4_size_sampled(dg):
+    """256^3 cells, order 4 (degree 3), driven subsonic turbulence, the
+    degree-3 configuration the benchmark runs: R at sampled cells against the
+    oracle in both precisions, then one mixed SSP-RK3 step with the energy
+    reset conserves mass to round-off."""
+    import torch
+    n, order, g = (256, 256, 256), 4, syn.GAMMA
+    s = dg.Solver(n, order, g, forcing=True)
+    fn = syn.solenoidal_velocity(seed=1234, mach=0.3, gamma=g)
+    s.project_fn(fn)
+    nv = syn.driving_modes(1.0, 2.0)
+    ah = np.random.default_rng(1234).normal(size=(len(nv), 6)) * 0.5
+    s.set_forcing(nv, ah)
+    w = s.get_state()
+    o = oracle.Oracle(n, order - 1, g)
+    o.set_forcing(nv, ah)
+    cells = syn.sample_cells(s.ncells, 200, seed=6)
+    Ro = o.rhs_cells(w, cells)
+    st, dt1 = o.cfl_dt(w, 1.0)
+    assert st == 0
+    w0max = np.abs(w.reshape(-1, 5, s.N)[:, :, 0]).max(axis=0)
+    del w
+    for prec, tol in ((dg.DG_PREC_FP64, TOL64), (dg.DG_PREC_MIXED, TOLMIX)):
+        s.set_precision(prec)
+        R = s.rhs().reshape(-1, 5, s.N)[cells]
+        for i in range(5):
+            scale = max(np.abs(Ro[:, i, :]).max(), w0max[i] / dt1)
+            assert np.abs(R[:, i, :] - Ro[:, i, :]).max() <= tol * scale, (prec, i)
+        del R
+    s.set_precision(dg.DG_PREC_MIXED)
+    t0 = s.totals()
+    s.step(s.cfl_dt(0.3))
+    s.energy_reset(math.sqrt(1.0 / g), 1.0)
+    s.check()
+    assert abs(s.totals()[0] - t0[0]) <= 1e-13 * abs(t0[0])
+    torch.cuda.synchronize()
+
+
 def test_error_codes(dg):
     g = syn.GAMMA
     s = dg.Solver((4, 4, 4), 3, g)
