@@ -90,6 +90,7 @@ def _load():
                 "orc_energy_reset_cells": (C.c_int, [P, dp, C.c_long, i64p, C.c_double,
                                                      C.c_double]),
                 "orc_totals": (None, [P, dp, dp]),
+                "orc_diagnostics": (None, [P, dp, dp]),
                 "orc_num_threads": (C.c_int, []),
             }
             for name, (res, args) in sig.items():
@@ -320,4 +321,11 @@ class Oracle:
     def totals(self, w):
         out = np.zeros(5)
         _load().orc_totals(C.byref(self._p), _dp(_f64(w)), _dp(out))
+        return out
+
+    def diagnostics(self, w):
+        """(rms Mach of the cell means, kinetic energy of the means,
+        injected power of the driving force)."""
+        out = np.zeros(3)
+        _load().orc_diagnostics(C.byref(self._p), _dp(_f64(w)), _dp(out))
         return out

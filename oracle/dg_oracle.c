@@ -891,3 +891,46 @@ void orc_totals(const orc_params* p, const double* w, double* out5) {
     out5[i] = s * vol;
   }
 }
+
+/* Sect. 4.1 (rms Mach number) and 4.2 (injected energy), readings in the
+ * header. */
+void orc_diagnostics(const orc_params* p, const double* w, double* out3) {
+  int k = p->k, N = orc_nmodes(k), Q = k + 1;
+  long nc = ncells(p);
+  double dx[3], vol = 1.0, V = 1.0;
+  for (int a = 0; a < 3; ++a) {
+    dx[a] = p->L[a] / p->n[a];
+    vol *= dx[a];
+    V *= p->L[a];
+  }
+  double g[MAXQ], gw[MAXQ];
+  orc_gauss(Q, g, gw);
+  double m2 = 0.0, kin = 0.0, pow_ = 0.0;
+  for (long c = 0; c < nc; ++c) {
+    const double* wK = w + c * 5 * N;
+    double rho = wK[0], m[3] = {wK[N], wK[2 * N], wK[3 * N]}, E = wK[4 * N];
+    double mm = m[0] * m[0] + m[1] * m[1] + m[2] * m[2];
+    double pr = (p->gamma - 1.0) * (E - 0.5 * mm / rho);
+    double vv = mm / (rho * rho);
+    m2 += vol * vv / (p->gamma * pr / rho);
+    kin += vol * 0.5 * mm / rho;
+    if (p->n_force > 0) {
+      int ijk[3];
+      cell_ijk(p, c, ijk);
+      for (int cz = 0; cz < Q; ++cz)
+        for (int b = 0; b < Q; ++b)
+          for (int a = 0; a < Q; ++a) {
+            double xi[3] = {g[a], g[b], g[cz]};
+            double x[3], acc[3], phi[MAXN], U[5];
+            for (int d = 0; d < 3; ++d) x[d] = (ijk[d] + 0.5) * dx[d] + 0.5 * dx[d] * xi[d];
+            forcing_at(p, x, acc);
+            orc_basis(k, xi, phi, NULL);
+            eval_at(k, wK, phi, U);
+            pow_ += vol * (U[1] * acc[0] + U[2] * acc[1] + U[3] * acc[2]) * gw[a] * gw[b] * gw[cz] / 8.0;
+          }
+    }
+  }
+  out3[0] = sqrt(m2 / V);
+  out3[1] = kin;
+  out3[2] = pow_;
+}

@@ -106,6 +106,15 @@ int orc_energy_reset_cells(const orc_params* p, double* w, long n_cells, const i
                            double c_iso, double rho0);
 /* sum_K |K| w_{i,0} */
 void orc_totals(const orc_params* p, const double* w, double* out5);
+
+/* Turbulence diagnostics of Sect. 4.1-4.2 (readings of the paper, which
+ * gives no formulas): out[0] = volume-weighted rms Mach number of the cell
+ * means, sqrt((1/V) sum_K |K| (|m/rho| / c)^2) with c^2 = gamma p / rho from
+ * the means; out[1] = kinetic energy of the means, sum_K |K| |m|^2 / (2 rho);
+ * out[2] = rate of work of the driving force (injected power),
+ * sum_K int_K m . a dV by the volume Gauss rule with the state polynomial
+ * (0 without forcing modes). */
+void orc_diagnostics(const orc_params* p, const double* w, double* out3);
 int orc_num_threads(void);
 
 #ifdef __cplusplus
