@@ -182,6 +182,17 @@ int dg_energy_reset(dg_ctx* ctx, double c_iso, double rho0, double* dissipated);
  * Synchronises. */
 int dg_totals(dg_ctx* ctx, double* out5);
 
+/* Turbulence diagnostics of the bound state (Sect. 4.1, rms Mach number;
+ * Sect. 4.2, injected energy; the paper gives no formulas, these are the
+ * readings): out3[0] = volume-weighted rms Mach number of the cell means,
+ * sqrt((1/V) sum_K |K| (|m|/rho / c)^2), c^2 = gamma p / rho from the means;
+ * out3[1] = kinetic energy of the cell means, sum_K |K| |m|^2 / (2 rho);
+ * out3[2] = power of the driving force, sum_K int_K m . a dV by the volume
+ * Gauss rule on the state polynomial and the cached driving field (0 without
+ * forcing); the energy it injects over a step of size dt is about
+ * out3[2] dt. Host array of 3 doubles. Synchronises; reports device errors. */
+int dg_diagnostics(dg_ctx* ctx, double* out3);
+
 /* Synchronise the bound stream and report (and clear) the device error
  * word. */
 int dg_check(dg_ctx* ctx);

@@ -60,6 +60,7 @@ _SIGS = {
     "dg_set_forcing": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "dg_energy_reset": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.POINTER(C.c_double)]),
     "dg_totals": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "dg_diagnostics": (C.c_int, [C.c_void_p, C.c_void_p]),
     "dg_check": (C.c_int, [C.c_void_p]),
     "dg_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
     "dg_kernel_stats": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -222,6 +223,12 @@ def dg_energy_reset(ctx, c_iso, rho0=1.0, want_dissipated=False):
     _check(load().dg_energy_reset(ctx, float(c_iso), float(rho0), C.byref(d) if want_dissipated else None),
            "dg_energy_reset")
     return d.value if want_dissipated else None
+
+
+def dg_diagnostics(ctx):
+    out = np.zeros(3)
+    _check(load().dg_diagnostics(ctx, out.ctypes.data), "dg_diagnostics")
+    return out
 
 
 def dg_totals(ctx):
@@ -432,6 +439,11 @@ class Solver:
 
     def totals(self):
         return dg_totals(self.ctx)
+
+    def diagnostics(self):
+        """(rms Mach of the cell means, kinetic energy of the means,
+        power of the driving force)."""
+        return dg_diagnostics(self.ctx)
 
     def check(self):
         dg_check(self.ctx)

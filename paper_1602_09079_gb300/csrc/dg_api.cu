@@ -865,6 +865,31 @@ int dg_energy_reset(dg_ctx* c, double c_iso, double rho0, double* dissipated) {
   return DG_OK;
 }
 
+int dg_diagnostics(dg_ctx* c, double* out3) {
+  DG_TRY(need_bound(c));
+  if (!out3) return DG_ERR_ARG;
+  DG_TRY(set_device(c));
+  long long nb = (c->geo.nc + 255) / 256;
+  const int G = (int)(nb < kRedBlocks ? nb : kRedBlocks);
+  const int force = c->n_force > 0 ? 1 : 0;
+  DG_TRY(launch(c, KC_OTHER, [&] {
+    return c->fn.diagnostics(c->prec, c->y, c->field, force, c->geo, c->part, G, c->stream);
+  }));
+  const double vol = c->geo.dx[0] * c->geo.dx[1] * c->geo.dx[2];
+  DG_TRY(launch(c, KC_OTHER, [&] {
+    sum_rows_kernel<<<3, 256, 0, c->stream>>>(c->part, G, vol, c->sums);
+    return cudaGetLastError();
+  }));
+  double h[3];
+  DG_CUDA(cudaMemcpyAsync(h, c->sums, sizeof(double) * 3, cudaMemcpyDeviceToHost, c->stream));
+  const int st = sync_and_check(c, nullptr);
+  if (st != DG_OK) return st;
+  out3[0] = std::sqrt(h[0] / (c->L[0] * c->L[1] * c->L[2]));
+  out3[1] = h[1];
+  out3[2] = h[2];
+  return DG_OK;
+}
+
 int dg_totals(dg_ctx* c, double* out5) {
   DG_TRY(need_bound(c));
   if (!out5) return DG_ERR_ARG;

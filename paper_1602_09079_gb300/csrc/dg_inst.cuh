@@ -239,6 +239,17 @@ cudaError_t reset_t(double* y, const Geo& g, double c2g, double inv_rho0, double
   return cudaGetLastError();
 }
 
+cudaError_t diagnostics(int prec, const double* y, const void* field, int force, const Geo& g, double* part, int nb,
+                        cudaStream_t s) {
+  if (prec)
+    diag_partial_kernel<KK, float><<<nb, 256, 0, s>>>(y, static_cast<const float*>(field), tab_ptr<double>(), g,
+                                                      force, part);
+  else
+    diag_partial_kernel<KK, double><<<nb, 256, 0, s>>>(y, static_cast<const double*>(field), tab_ptr<double>(), g,
+                                                       force, part);
+  return cudaGetLastError();
+}
+
 cudaError_t energy_reset(int prec, double* y, const Geo& g, double c2g, double inv_rho0, double* part, int* n_part,
                          int* list, Ctrl* ctrl, float* yf, cudaStream_t s) {
   return prec ? reset_t<float>(y, g, c2g, inv_rho0, part, n_part, list, ctrl, yf, s)
@@ -280,6 +291,7 @@ Launchers DG_PASTE(launchers_k, DG_K)() {
   L.screen = screen;
   L.cfl = cfl;
   L.energy_reset = energy_reset;
+  L.diagnostics = diagnostics;
   L.project = project;
   L.forcing_field = forcing_field;
   L.tab64 = tab_ptr<double>;

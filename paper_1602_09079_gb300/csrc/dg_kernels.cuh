@@ -1601,6 +1601,64 @@ __global__ void __launch_bounds__(kThreads) project_kernel(const double* __restr
 // a(x_q) = sum_j Re a_j cos(k_j.x) - Im a_j sin(k_j.x), k_j = 2 pi n_j / L
 // (Sect. 3.1), cached at every volume point: field[(d*Q3 + q)*nc + c].
 // modes: [n][9] = n_x, n_y, n_z (as doubles), Re a (3), Im a (3).
+// Turbulence diagnostics (Sect. 4.1 rms Mach number, Sect. 4.2 injected
+// energy): per-block partial sums, in a fixed order, of the per-cell
+// (|m|/rho / c)^2 and |m|^2/(2 rho) of the cell means and, with forcing, the
+// injected power density sum_q (m . a)(xi_q) omega_q / 8 (the state
+// polynomial's momentum at the volume Gauss points times the cached driving
+// field). part[j * gridDim.x + b], j = 0, 1, 2.
+template <int K, typename T>
+__global__ void __launch_bounds__(256) diag_partial_kernel(const double* __restrict__ y, const T* __restrict__ field,
+                                                           const double* __restrict__ tab64, Geo g, int force,
+                                                           double* __restrict__ part) {
+  using TB = Tab<K>;
+  constexpr int N = TB::N, Q3 = TB::Q3;
+  __shared__ double s[3][256];
+  const long long nc = g.nc;
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (long long c = (long long)blockIdx.x * 256 + threadIdx.x; c < nc; c += (long long)gridDim.x * 256) {
+    const double rho = y[c], E = y[(size_t)4 * N * nc + c];
+    double m[3], mm = 0.0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      m[d] = y[(size_t)(1 + d) * N * nc + c];
+      mm += m[d] * m[d];
+    }
+    const double pr = (g.gamma - 1.0) * (E - 0.5 * mm / rho);
+    acc[0] += (mm / (rho * rho)) / (g.gamma * pr / rho);
+    acc[1] += 0.5 * mm / rho;
+    if (force) {
+      double w[3][N];
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int l = 0; l < N; ++l) w[d][l] = y[(size_t)((1 + d) * N + l) * nc + c];
+      double pw = 0.0;
+      for (int q = 0; q < Q3; ++q) {
+        const double* ph = tab64 + TB::VPHIW + q * N;  // phi_l omega_q / 8
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          double md = 0.0;
+#pragma unroll
+          for (int l = 0; l < N; ++l) md += w[d][l] * __ldg(ph + l);
+          pw += md * (double)field[((size_t)d * Q3 + q) * nc + c];
+        }
+      }
+      acc[2] += pw;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 3; ++j) s[j][threadIdx.x] = acc[j];
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) s[j][threadIdx.x] += s[j][threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x < 3) part[threadIdx.x * gridDim.x + blockIdx.x] = s[threadIdx.x][0];
+}
+
 template <int K, typename T>
 __global__ void __launch_bounds__(kThreads) forcing_field_kernel(T* __restrict__ field, const double* __restrict__ modes,
                                                                  int n_modes, const double* __restrict__ tab64, Geo g,

@@ -47,6 +47,11 @@ struct Launchers {
   cudaError_t (*project)(const double* f, double* y, const Geo& g, long long first, long long count, cudaStream_t s);
   cudaError_t (*forcing_field)(int prec, void* field, const double* modes, int n_modes, const Geo& g,
                                const double* L, cudaStream_t s);
+  // per-block partial sums of the turbulence diagnostics into part[3 * nb]
+  // (field: the cached driving field in the precision prec selects, or
+  // ignored when force == 0)
+  cudaError_t (*diagnostics)(int prec, const double* y, const void* field, int force, const Geo& g, double* part,
+                             int nb, cudaStream_t s);
   // the degree's FP64 table on the current device
   const double* (*tab64)();
   size_t table_size;
