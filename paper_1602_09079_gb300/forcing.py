@@ -17,6 +17,21 @@ import math
 import numpy as np
 
 
+def half_space_modes(nmin=1.0, nmax=2.0):
+    """Integer wave vectors n with nmin <= |n| <= nmax, one of each +-n pair
+    (first nonzero component positive), in lexicographic order."""
+    r = int(math.floor(nmax))
+    out = []
+    for a in range(-r, r + 1):
+        for b in range(-r, r + 1):
+            for c in range(-r, r + 1):
+                m = math.sqrt(a * a + b * b + c * c)
+                first = a if a != 0 else (b if b != 0 else c)
+                if first > 0 and nmin - 1e-12 <= m <= nmax + 1e-12:
+                    out.append((a, b, c))
+    return np.array(out, dtype=np.int32)
+
+
 def paraboloid(nmag, nmin=1.0, nmax=2.0):
     """Mode amplitude: 1 at the centre (nmin+nmax)/2, 0 at both ends."""
     c = 0.5 * (nmin + nmax)
