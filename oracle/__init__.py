@@ -47,9 +47,10 @@ class Params(C.Structure):
     _fields_ = [("k", C.c_int), ("n", C.c_int * 3), ("L", C.c_double * 3),
                 ("gamma", C.c_double), ("eps_rho", C.c_double), ("eps_p", C.c_double),
                 ("n_force", C.c_int), ("force_n", C.POINTER(C.c_int32)),
-                ("force_a", C.POINTER(C.c_double)), ("flux", C.c_int)]
+                ("force_a", C.POINTER(C.c_double)), ("flux", C.c_int), ("limiter_points", C.c_int)]
 
 FLUX_HLLC, FLUX_EXACT = 0, 1
+LIMIT_S, LIMIT_S_VOLUME = 0, 1
 
 
 def _load():
@@ -192,7 +193,8 @@ class Oracle:
     """One periodic Cartesian mesh, degree k, ideal gas gamma, optional
     forcing modes; every method takes and returns canonical-layout arrays."""
 
-    def __init__(self, n, k, gamma, L=(1.0, 1.0, 1.0), eps_rho=1e-12, eps_p=1e-12, flux=FLUX_HLLC):
+    def __init__(self, n, k, gamma, L=(1.0, 1.0, 1.0), eps_rho=1e-12, eps_p=1e-12, flux=FLUX_HLLC,
+                 limiter_points=LIMIT_S):
         self.n = tuple(int(v) for v in n)
         self.k = int(k)
         self.N = nmodes(self.k)
@@ -212,6 +214,7 @@ class Oracle:
         self._p.eps_p = eps_p
         self._p.n_force = 0
         self._p.flux = int(flux)
+        self._p.limiter_points = int(limiter_points)
         self._p.force_n = self._force_n.ctypes.data_as(C.POINTER(C.c_int32))
         self._p.force_a = _dp(self._force_a)
 

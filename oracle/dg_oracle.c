@@ -162,6 +162,7 @@ static int check_params(const orc_params* p) {
     if (p->n[a] < 1 || !(p->L[a] > 0)) return ORC_ERR_ARG;
   if (!(p->gamma > 1.0)) return ORC_ERR_ARG;
   if (p->n_force < 0 || (p->n_force > 0 && (!p->force_n || !p->force_a))) return ORC_ERR_ARG;
+  if (p->limiter_points != ORC_LIMIT_S && p->limiter_points != ORC_LIMIT_S_VOLUME) return ORC_ERR_ARG;
   return ORC_OK;
 }
 
@@ -719,10 +720,26 @@ static int limit_cell(const orc_params* p, double* wK, const double* pts, int np
 static int limit_list(const orc_params* p, double* w, long n, const int64_t* cells, int8_t* flags,
                       int64_t* nlim) {
   int k = p->k, N = orc_nmodes(k), Q = k + 1, m = orc_gll_count(k);
-  int npts = 3 * m * Q * Q;
+  int nS = 3 * m * Q * Q;
+  /* optional: the volume Gauss points, where the volume fluxes are
+   * evaluated, join S (Sect. 2.5 asks that S contain every point where
+   * fluxes are evaluated; S itself covers the face points only) */
+  int npts = nS + (p->limiter_points == ORC_LIMIT_S_VOLUME ? Q * Q * Q : 0);
   double* pts = (double*)malloc(sizeof(double) * 3 * npts);
   double* phis = (double*)malloc(sizeof(double) * npts * N);
   limiter_points(k, pts);
+  if (npts > nS) {
+    double g[MAXQ], gw[MAXQ];
+    orc_gauss(Q, g, gw);
+    int s = nS;
+    for (int c = 0; c < Q; ++c)
+      for (int b = 0; b < Q; ++b)
+        for (int a = 0; a < Q; ++a, ++s) {
+          pts[3 * s] = g[a];
+          pts[3 * s + 1] = g[b];
+          pts[3 * s + 2] = g[c];
+        }
+  }
   for (int s = 0; s < npts; ++s) orc_basis(k, pts + 3 * s, phis + s * N, NULL);
   int status = ORC_OK;
   int64_t count = 0;

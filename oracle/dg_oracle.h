@@ -46,7 +46,11 @@ typedef struct {
   const int32_t* force_n;   /* 3*n_force integer wave vectors n, k = 2 pi n / L */
   const double* force_a;    /* 6*n_force: Re a_x,a_y,a_z, Im a_x,a_y,a_z */
   int flux;           /* numerical flux: ORC_FLUX_HLLC or ORC_FLUX_EXACT */
+  int limiter_points; /* ORC_LIMIT_S (the paper's S) or ORC_LIMIT_S_VOLUME
+                         (S and the (k+1)^3 volume Gauss points) */
 } orc_params;
+
+enum { ORC_LIMIT_S = 0, ORC_LIMIT_S_VOLUME = 1 };
 
 enum { ORC_FLUX_HLLC = 0, ORC_FLUX_EXACT = 1 };
 
