@@ -155,6 +155,17 @@ int dg_set_precision(dg_ctx* ctx, int mode);
  * converge makes the next synchronising call return DG_ERR_NEWTON). Any
  * other value: DG_ERR_ARG. Applies to dg_rhs, dg_step and the indicator
  * capture from the next call on. */
+/* Point set of the positivity limiter (Sect. 2.5, which asks that it
+ * contain every point where fluxes are evaluated): DG_LIMIT_S (default) is
+ * S = S_x u S_y u S_z as the paper writes it, which covers the face
+ * quadrature points but not the interior volume Gauss points;
+ * DG_LIMIT_S_VOLUME adds the (k+1)^3 volume Gauss points (theta1 and theta2
+ * over the union, and the screens use max |phi_l| over the union). Any other
+ * value: DG_ERR_ARG. The next dg_step limits its input again. */
+#define DG_LIMIT_S 0
+#define DG_LIMIT_S_VOLUME 1
+int dg_set_limiter_points(dg_ctx* ctx, int mode);
+
 #define DG_FLUX_HLLC 0
 #define DG_FLUX_EXACT 1
 int dg_set_flux(dg_ctx* ctx, int flux);

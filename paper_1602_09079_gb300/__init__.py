@@ -22,6 +22,7 @@ DG_OK, DG_ERR_ARG, DG_ERR_NOT_BOUND, DG_ERR_CUDA = 0, -1, -2, -3
 DG_ERR_NONFINITE, DG_ERR_POSITIVITY, DG_ERR_NEWTON, DG_ERR_TOO_LARGE = -4, -5, -6, -7
 DG_PREC_FP64, DG_PREC_MIXED = 0, 1
 DG_FLUX_HLLC, DG_FLUX_EXACT = 0, 1
+DG_LIMIT_S, DG_LIMIT_S_VOLUME = 0, 1
 DG_FEATURE_FORCING = 1
 
 _lock = threading.Lock()
@@ -56,6 +57,7 @@ _SIGS = {
     "dg_cfl_dt": (C.c_int, [C.c_void_p, C.c_double, C.POINTER(C.c_double)]),
     "dg_set_precision": (C.c_int, [C.c_void_p, C.c_int]),
     "dg_set_flux": (C.c_int, [C.c_void_p, C.c_int]),
+    "dg_set_limiter_points": (C.c_int, [C.c_void_p, C.c_int]),
     "dg_set_eps": (C.c_int, [C.c_void_p, C.c_double, C.c_double]),
     "dg_set_forcing": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "dg_energy_reset": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.POINTER(C.c_double)]),
@@ -199,6 +201,10 @@ def dg_cfl_dt(ctx, courant):
 
 def dg_set_precision(ctx, mode):
     _check(load().dg_set_precision(ctx, int(mode)), "dg_set_precision")
+
+
+def dg_set_limiter_points(ctx, mode):
+    _check(load().dg_set_limiter_points(ctx, int(mode)), "dg_set_limiter_points")
 
 
 def dg_set_flux(ctx, flux):
@@ -427,6 +433,9 @@ class Solver:
 
     def set_flux(self, flux):
         dg_set_flux(self.ctx, flux)
+
+    def set_limiter_points(self, mode):
+        dg_set_limiter_points(self.ctx, mode)
 
     def set_eps(self, eps_rho, eps_p):
         dg_set_eps(self.ctx, eps_rho, eps_p)

@@ -160,6 +160,12 @@ void build_tables(double* t) {
           ++n;
         }
   }
+  // max of |phi_l| over S and the volume Gauss points (the optional point set)
+  for (int l = 0; l < N; ++l) {
+    double mv = t[TB::LMAX + l];
+    for (int q = 0; q < TB::Q3; ++q) mv = std::fmax(mv, std::fabs(t[TB::VPHI + q * N + l]));
+    t[TB::LMAXV + l] = mv;
+  }
   for (int t2 = 0; t2 < Q; ++t2)
     for (int t1 = 0; t1 < Q; ++t1) {
       int j = 0;
@@ -788,6 +794,13 @@ int dg_set_precision(dg_ctx* c, int mode) {
     DG_TRY(set_device(c));
     DG_TRY(refresh_field(c));
   }
+  return DG_OK;
+}
+
+int dg_set_limiter_points(dg_ctx* c, int mode) {
+  if (!c || (mode != DG_LIMIT_S && mode != DG_LIMIT_S_VOLUME)) return DG_ERR_ARG;
+  c->geo.lim_vol = mode == DG_LIMIT_S_VOLUME ? 1 : 0;
+  c->limited = false;
   return DG_OK;
 }
 

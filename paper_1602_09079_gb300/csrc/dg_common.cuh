@@ -80,7 +80,9 @@ struct Tab {
   // 1D Gauss nodes and weights, [Q] each
   static constexpr int GX = D1W + (K + 1) * Q;
   static constexpr int GW = GX + Q;
-  static constexpr int SIZE = GW + Q;
+  // max over S and the volume Gauss points of |phi_l|, [N]
+  static constexpr int LMAXV = GW + Q;
+  static constexpr int SIZE = LMAXV + N;
 };
 constexpr int TAB_STRIDE = 16384;  // >= Tab<3>::SIZE
 static_assert(Tab<3>::SIZE <= TAB_STRIDE, "table stride");
@@ -112,6 +114,7 @@ struct Geo {
   double inv_dx[3];
   double gamma;
   double eps_rho, eps_p;
+  int lim_vol;  // limiter point set: 0 = S, 1 = S and the volume Gauss points
 };
 
 // --------------------------------------------------------------- physics
@@ -457,7 +460,7 @@ __device__ __forceinline__ double positivity_tau(const double* qb, const double*
 // Returns flag bits (1: theta1 < 1, 2: theta2 < 1) and ORs errors into err.
 template <int K>
 __device__ int limit_cell(double* w, long long stride, const double* __restrict__ tab, double gamma,
-                          double eps_r, double eps_p, unsigned* err) {
+                          double eps_r, double eps_p, unsigned* err, int vol) {
   using TB = Tab<K>;
   constexpr int N = TB::N;
   const double gm1 = gamma - 1.0;
@@ -476,8 +479,11 @@ __device__ int limit_cell(double* w, long long stride, const double* __restrict_
     return 0;
   }
   if (N == 1) return 0;
-  const double* lmax = tab + TB::LMAX;
+  const double* lmax = tab + (vol ? TB::LMAXV : TB::LMAX);
   const double* lphi = tab + TB::LPHI;
+  const double* vphi = tab + TB::VPHI;
+  // the point set: S (TB::NL points), then optionally the volume Gauss points
+  const int npts = TB::NL + (vol ? TB::Q3 : 0);
   double sabs[5];
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
@@ -491,10 +497,11 @@ __device__ int limit_cell(double* w, long long stride, const double* __restrict_
   bool rho_safe = rlo >= eps_r + 1e-13 * (fabs(mean[0]) + sabs[0]);
   if (!rho_safe) {
     double rmin = mean[0];
-    for (int s = 0; s < TB::NL; ++s) {
+    for (int s = 0; s < npts; ++s) {
+      const double* ph = s < TB::NL ? lphi + s * N : vphi + (s - TB::NL) * N;
       double r = 0.0;
 #pragma unroll
-      for (int l = 0; l < N; ++l) r += w[l * stride] * __ldg(lphi + s * N + l);
+      for (int l = 0; l < N; ++l) r += w[l * stride] * __ldg(ph + l);
       rmin = fmin(rmin, r);
     }
     if (rmin < eps_r) {
@@ -522,13 +529,14 @@ __device__ int limit_cell(double* w, long long stride, const double* __restrict_
   if (!p_safe) {
     double th2 = 1.0;
     bool newton_fail = false;
-    for (int s = 0; s < TB::NL; ++s) {
+    for (int s = 0; s < npts; ++s) {
+      const double* ph = s < TB::NL ? lphi + s * N : vphi + (s - TB::NL) * N;
       double U[5];
 #pragma unroll
       for (int i = 0; i < 5; ++i) {
         double acc = 0.0;
 #pragma unroll
-        for (int l = 0; l < N; ++l) acc += w[(i * N + l) * stride] * __ldg(lphi + s * N + l);
+        for (int l = 0; l < N; ++l) acc += w[(i * N + l) * stride] * __ldg(ph + l);
         U[i] = acc;
       }
       double p = gm1 * (U[4] - 0.5 * (U[1] * U[1] + U[2] * U[2] + U[3] * U[3]) / U[0]);

@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(kThreads) volume_kernel(const double* __restri
       for (int i = 0; i < 5; ++i) {
         m[i] = sY[(i * N) * C + tid];
         double sa = 0.0;
-        for (int l = 1; l < N; ++l) sa += fabs(sY[(i * N + l) * C + tid]) * __ldg(tab64 + TB::LMAX + l);
+        for (int l = 1; l < N; ++l) sa += fabs(sY[(i * N + l) * C + tid]) * __ldg(tab64 + (g.lim_vol ? TB::LMAXV : TB::LMAX) + l);
         a[i] = sa;
         for (int l = 0; l < N; ++l) fin &= isfinite(sY[(i * N + l) * C + tid]);
       }
@@ -664,7 +664,7 @@ __global__ void __launch_bounds__(VolF32<K>::THREADS, VolF32<K>::MINB) volume_f3
       st.yf[a] = vf;
       finite &= finite64(v);
       if (l == 0) mean = v;
-      else sabsf += fabsf(vf) * c_tab32[TB::LMAX + l];
+      else sabsf += fabsf(vf) * (g.lim_vol ? c_tab32[TB::LMAXV + l] : c_tab32[TB::LMAX + l]);
     }
   }
   // the screen's excursion sums are taken in FP32 from the rounded values
@@ -706,7 +706,7 @@ __global__ void __launch_bounds__(kThreads) limit_list_kernel(double* __restrict
   unsigned e = 0;
   for (unsigned i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) {
     const long long cell = list[i];
-    if (limit_cell<K>(y + cell, g.nc, tab64, g.gamma, g.eps_rho, g.eps_p, &e) && yf)
+    if (limit_cell<K>(y + cell, g.nc, tab64, g.gamma, g.eps_rho, g.eps_p, &e, g.lim_vol) && yf)
       for (int r = 0; r < 5 * N; ++r) yf[(size_t)r * g.nc + cell] = (float)y[(size_t)r * g.nc + cell];
   }
   if (e) atomicOr(&ctrl->err, e);
@@ -728,7 +728,7 @@ __global__ void __launch_bounds__(kThreads) screen_kernel(const double* __restri
     double sa = 0.0;
     for (int l = 1; l < N; ++l) {
       const double v = y[(size_t)(i * N + l) * g.nc + cell];
-      sa += fabs(v) * __ldg(tab64 + Tab<K>::LMAX + l);
+      sa += fabs(v) * __ldg(tab64 + (g.lim_vol ? Tab<K>::LMAXV : Tab<K>::LMAX) + l);
       fin &= isfinite(v);
     }
     fin &= isfinite(m[i]);
@@ -1002,7 +1002,7 @@ __global__ void __launch_bounds__(kThreads) volume_sf_kernel(const double* __res
     double sa = 0.0;
     bool fin = isfinite(row[0]);
     for (int l = 1; l < N; ++l) {
-      sa += fabs(row[l * C]) * __ldg(tab64 + TB::LMAX + l);
+      sa += fabs(row[l * C]) * __ldg(tab64 + (g.lim_vol ? TB::LMAXV : TB::LMAX) + l);
       fin &= isfinite(row[l * C]);
     }
     sM[it] = fin ? row[0] : __longlong_as_double(0x7ff8000000000000LL);
@@ -1316,7 +1316,7 @@ __global__ void __launch_bounds__(kThreads) volume_sfb_kernel(const double* __re
     double sa = 0.0;
     bool fin = isfinite(row[0]);
     for (int l = 1; l < N; ++l) {
-      sa += fabs(row[l * C]) * __ldg(tab64 + TB::LMAX + l);
+      sa += fabs(row[l * C]) * __ldg(tab64 + (g.lim_vol ? TB::LMAXV : TB::LMAX) + l);
       fin &= isfinite(row[l * C]);
     }
     sM[it] = fin ? row[0] : __longlong_as_double(0x7ff8000000000000LL);
@@ -1353,7 +1353,7 @@ __global__ void __launch_bounds__(kThreads) limit_kernel(double* __restrict__ y,
   const long long cell = (long long)blockIdx.x * kThreads + threadIdx.x;
   if (cell < g.nc) {
     unsigned e = 0;
-    int f = limit_cell<K>(y + cell, g.nc, tab64, g.gamma, g.eps_rho, g.eps_p, &e);
+    int f = limit_cell<K>(y + cell, g.nc, tab64, g.gamma, g.eps_rho, g.eps_p, &e, g.lim_vol);
     if (flags) flags[cell] = (int8_t)f;
     if (f) atomicAdd(&s_cnt, 1u);
     if (e) atomicOr(&s_err, e);
@@ -1516,14 +1516,14 @@ __global__ void __launch_bounds__(kThreads) energy_reset_kernel(double* __restri
 #pragma unroll
         for (int l = 1; l < N; ++l) {
           const float v = i < 4 ? (float)sW[(i * N + l) * C + c] : f64_to_f32(sEn[l * C + c]);
-          sf += fabsf(v) * c_tab32[TB::LMAX + l];
+          sf += fabsf(v) * (g.lim_vol ? c_tab32[TB::LMAXV + l] : c_tab32[TB::LMAX + l]);
           fin &= isfinite(v);
         }
         sa = (double)sf * (1.0 + 1e-5);
       } else {
         for (int l = 1; l < N; ++l) {
           const double v = i < 4 ? __ldg(y + (size_t)(i * N + l) * nc + cell) : sEn[l * C + c];
-          sa += fabs(v) * __ldg(tab64 + TB::LMAX + l);
+          sa += fabs(v) * __ldg(tab64 + (g.lim_vol ? TB::LMAXV : TB::LMAX) + l);
           fin &= isfinite(v);
         }
       }
