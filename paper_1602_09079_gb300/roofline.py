@@ -3,9 +3,12 @@
 Per cell and per RK stage (k = degree, N = N(k), Q = k+1, Q2 = Q^2,
 Q3 = Q^3; FMA = 2 flops; sqrt and division count as one flop each):
 
-face_flux_kernel (3 faces per cell, Q2 points each)
+faces, dense count (3 faces per cell, Q2 points each; face_flops)
     traces of both sides  2 x 5 x N FMA           -> 20 N
     HLLC flux                                      -> HLLC_FLOPS
+face_sf64_kernel (sum-factorised traces; face_sf_flops)
+    normal contraction    2 x 5 N FMA per face
+    tangential expansion  2 x 5 (Q T + Q2 (k+1)) FMA per face, then HLLC
 volume_sf_kernel (sum factorisation; T = (k+1)(k+2)/2, KP = k+1)
     point values          5 (Q N + Q2 T + Q3 KP) FMA
     Euler fluxes, scaling Q3 x 46;   source  Q3 x 12 (forcing only)
