@@ -92,6 +92,7 @@ def _load():
                                                      C.c_double]),
                 "orc_totals": (None, [P, dp, dp]),
                 "orc_diagnostics": (None, [P, dp, dp]),
+                "orc_sample_velocity": (C.c_int, [P, dp, C.c_int, C.c_int, dp]),
                 "orc_num_threads": (C.c_int, []),
             }
             for name, (res, args) in sig.items():
@@ -325,6 +326,30 @@ class Oracle:
         out = np.zeros(5)
         _load().orc_totals(C.byref(self._p), _dp(_f64(w)), _dp(out))
         return out
+
+    def sample_velocity(self, w, sub, comp):
+        """Velocity component on the (n sub)^3 sub-cell-centre grid,
+        array [Z][Y][X]."""
+        M = self.n[0] * sub
+        out = np.zeros((M, M, M))
+        assert self._call("orc_sample_velocity", _dp(_f64(w)), int(sub), int(comp), _dp(out)) == OK
+        return out
+
+    def velocity_spectrum(self, w, sub):
+        """Sect. 3.3: E[b] = sum over integer wave vectors with round(|n|) = b
+        of |v_hat(n)|^2 / M^6, summed over the three velocity components (the
+        unnormalised DFT of the sampled field by numpy; sum_b E[b] is the
+        mean square of the samples by Parseval)."""
+        M = self.n[0] * sub
+        nb = int(np.floor(np.sqrt(3.0) * M / 2.0)) + 2
+        f = np.fft.fftfreq(M, 1.0 / M)
+        kz, ky, kx = np.meshgrid(f, f, f, indexing="ij")
+        b = np.floor(np.sqrt(kx ** 2 + ky ** 2 + kz ** 2) + 0.5).astype(np.int64)
+        E = np.zeros(nb)
+        for comp in range(3):
+            vh = np.fft.fftn(self.sample_velocity(w, sub, comp))
+            E += np.bincount(b.ravel(), weights=(np.abs(vh) ** 2).ravel(), minlength=nb)[:nb] / float(M) ** 6
+        return E
 
     def diagnostics(self, w):
         """(rms Mach of the cell means, kinetic energy of the means,

@@ -951,3 +951,22 @@ void orc_diagnostics(const orc_params* p, const double* w, double* out3) {
   out3[1] = kin;
   out3[2] = pow_;
 }
+
+/* Sect. 3.3: the velocity field sampled below the cell size for spectra. */
+int orc_sample_velocity(const orc_params* p, const double* w, int sub, int comp, double* out) {
+  if (check_params(p) || sub < 1 || comp < 0 || comp > 2) return ORC_ERR_ARG;
+  if (p->n[0] != p->n[1] || p->n[1] != p->n[2]) return ORC_ERR_ARG;
+  int n = p->n[0], M = n * sub;
+#pragma omp parallel for schedule(static)
+  for (long Z = 0; Z < M; ++Z)
+    for (long Y = 0; Y < M; ++Y)
+      for (long X = 0; X < M; ++X) {
+        double xi[3] = {-1.0 + (2.0 * (X % sub) + 1.0) / sub, -1.0 + (2.0 * (Y % sub) + 1.0) / sub,
+                        -1.0 + (2.0 * (Z % sub) + 1.0) / sub};
+        long cell = ((Z / sub) * n + Y / sub) * n + X / sub;
+        double U[5];
+        orc_eval(p, w, cell, xi, U);
+        out[(Z * M + Y) * M + X] = U[1 + comp] / U[0];
+      }
+  return ORC_OK;
+}

@@ -119,6 +119,12 @@ void orc_totals(const orc_params* p, const double* w, double* out5);
  * sum_K int_K m . a dV by the volume Gauss rule with the state polynomial
  * (0 without forcing modes). */
 void orc_diagnostics(const orc_params* p, const double* w, double* out3);
+
+/* Velocity component comp (0..2) of the state polynomial, m_comp / rho, at
+ * the centres of sub^3 equal sub-cells of every cell of a cubic mesh
+ * (Sect. 3.3 spectra sample the solution below the cell size): out [M][M][M]
+ * with M = n sub, last index along x. */
+int orc_sample_velocity(const orc_params* p, const double* w, int sub, int comp, double* out);
 int orc_num_threads(void);
 
 #ifdef __cplusplus
