@@ -204,6 +204,23 @@ int dg_totals(dg_ctx* ctx, double* out5);
  * out3[2] dt. Host array of 3 doubles. Synchronises; reports device errors. */
 int dg_diagnostics(dg_ctx* ctx, double* out3);
 
+/* Velocity power spectrum of the bound state (Sect. 3.3): the velocity
+ * m/rho of the state polynomial is sampled at the centres of sub^3 equal
+ * sub-cells of every cell (an M^3 grid, M = n sub), each component is
+ * transformed by a 3D real-to-complex FFT (cuFFT), and the power of every
+ * integer wave vector n (k = 2 pi n / L) is added to shell round(|n|):
+ * spectrum[b] = sum_{round(|n|) = b} |v_hat(n)|^2 / M^6 over the three
+ * components, so that sum_b spectrum[b] = mean |v|^2 over the samples (the
+ * normalisation that makes the spectrum integrate to the total, as the
+ * paper asks). Cubic meshes of a cubic box only (else DG_ERR_ARG); 1 <= sub
+ * <= 8. dg_spectrum_sizes gives the device work-area bytes the caller
+ * allocates (bins, one real grid, one complex half spectrum, cuFFT's work
+ * area; DG_ERR_TOO_LARGE if cuFFT cannot plan the size) and the number of
+ * bins, floor(sqrt(3) M / 2) + 2. spectrum: host array of n_bins doubles.
+ * Synchronises. */
+int dg_spectrum_sizes(const dg_ctx* ctx, int sub, size_t* work_bytes, int* n_bins);
+int dg_velocity_spectrum(dg_ctx* ctx, int sub, void* work_dev, size_t work_bytes, double* spectrum);
+
 /* Synchronise the bound stream and report (and clear) the device error
  * word. */
 int dg_check(dg_ctx* ctx);

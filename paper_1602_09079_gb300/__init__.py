@@ -63,6 +63,8 @@ _SIGS = {
     "dg_energy_reset": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.POINTER(C.c_double)]),
     "dg_totals": (C.c_int, [C.c_void_p, C.c_void_p]),
     "dg_diagnostics": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "dg_spectrum_sizes": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_size_t), C.POINTER(C.c_int)]),
+    "dg_velocity_spectrum": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t, C.c_void_p]),
     "dg_check": (C.c_int, [C.c_void_p]),
     "dg_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
     "dg_kernel_stats": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -234,6 +236,19 @@ def dg_energy_reset(ctx, c_iso, rho0=1.0, want_dissipated=False):
 def dg_diagnostics(ctx):
     out = np.zeros(3)
     _check(load().dg_diagnostics(ctx, out.ctypes.data), "dg_diagnostics")
+    return out
+
+
+def dg_spectrum_sizes(ctx, sub):
+    b, nb = C.c_size_t(0), C.c_int(0)
+    _check(load().dg_spectrum_sizes(ctx, int(sub), C.byref(b), C.byref(nb)), "dg_spectrum_sizes")
+    return b.value, nb.value
+
+
+def dg_velocity_spectrum(ctx, sub, work, work_bytes, n_bins):
+    out = np.zeros(n_bins)
+    _check(load().dg_velocity_spectrum(ctx, int(sub), _ptr(work), int(work_bytes), out.ctypes.data),
+           "dg_velocity_spectrum")
     return out
 
 
@@ -448,6 +463,13 @@ class Solver:
 
     def totals(self):
         return dg_totals(self.ctx)
+
+    def velocity_spectrum(self, sub=4):
+        """Shell-summed velocity power spectrum on sub^3 samples per cell
+        (work area allocated with torch for the call)."""
+        nbytes, nb = dg_spectrum_sizes(self.ctx, sub)
+        work = self.torch.empty(nbytes, dtype=self.torch.uint8, device=self.device)
+        return dg_velocity_spectrum(self.ctx, sub, work, nbytes, nb)
 
     def diagnostics(self):
         """(rms Mach of the cell means, kinetic energy of the means,

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libdg_gb300.so")
-UNITS = ["dg_api.cu", "dg_k0.cu", "dg_k1.cu", "dg_k2.cu", "dg_k3.cu", "dg_mlp.cu"]
+UNITS = ["dg_api.cu", "dg_k0.cu", "dg_k1.cu", "dg_k2.cu", "dg_k3.cu", "dg_mlp.cu", "dg_spectrum.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 
@@ -65,7 +65,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
         objs = list(ex.map(compile_one, UNITS))
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nv, *ARCH, "-shared", "-o", tmp, *objs]
+    cmd = [nv, *ARCH, "-shared", "-o", tmp, *objs, "-lcufft"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -13,6 +13,7 @@
 #include "dg.h"
 #include "dg_launch.h"
 #include "dg_mlp.h"
+#include "dg_spectrum.h"
 
 using namespace dg;
 
@@ -900,6 +901,41 @@ int dg_diagnostics(dg_ctx* c, double* out3) {
   out3[0] = std::sqrt(h[0] / (c->L[0] * c->L[1] * c->L[2]));
   out3[1] = h[1];
   out3[2] = h[2];
+  return DG_OK;
+}
+
+namespace {
+int spectrum_args(const dg_ctx* c, int sub, int* M) {
+  if (!c || sub < 1 || sub > 8) return DG_ERR_ARG;
+  const Geo& g = c->geo;
+  if (g.nx != g.ny || g.ny != g.nz || c->L[0] != c->L[1] || c->L[1] != c->L[2]) return DG_ERR_ARG;
+  *M = g.nx * sub;
+  return DG_OK;
+}
+}  // namespace
+
+int dg_spectrum_sizes(const dg_ctx* c, int sub, size_t* work_bytes, int* n_bins) {
+  int M = 0;
+  DG_TRY(spectrum_args(c, sub, &M));
+  if (!work_bytes || !n_bins) return DG_ERR_ARG;
+  DG_TRY(set_device(c));
+  const size_t b = dg::spec::work_bytes(M);
+  if (b == 0) return DG_ERR_TOO_LARGE;
+  *work_bytes = b;
+  *n_bins = dg::spec::n_bins(M);
+  return DG_OK;
+}
+
+int dg_velocity_spectrum(dg_ctx* c, int sub, void* work_dev, size_t work_bytes, double* spectrum) {
+  DG_TRY(need_bound(c));
+  int M = 0;
+  DG_TRY(spectrum_args(c, sub, &M));
+  if (!work_dev || !spectrum) return DG_ERR_ARG;
+  DG_TRY(set_device(c));
+  int cst = 0;
+  DG_CUDA(dg::spec::velocity_spectrum(c->k, c->y, c->geo.nx, sub, work_dev, work_bytes, spectrum, c->stream, &cst));
+  if (cst == -1) return DG_ERR_ARG;
+  if (cst != 0) return DG_ERR_CUDA;
   return DG_OK;
 }
 

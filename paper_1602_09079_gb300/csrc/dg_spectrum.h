@@ -1,0 +1,28 @@
+// dg_spectrum.h -- velocity power spectrum of the state (arXiv:1602.09079,
+// Sect. 3.3): the state polynomial's velocity sampled on sub^3 points per
+// cell, a 3D real-to-complex FFT per component (cuFFT), shell sums of the
+// power. Called by the C ABI (dg_api.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+namespace dg {
+namespace spec {
+
+// bins: floor(sqrt(3) M / 2) + 2 for the M = n * sub points per axis
+int n_bins(int M);
+
+// device bytes the caller provides: bins, one real M^3 grid, one complex
+// half-spectrum and cuFFT's work area; 0 if cuFFT cannot plan the size
+size_t work_bytes(int M);
+
+// E(bin) = sum over wave vectors with round(|n|) = bin of |v_hat(n)|^2 / M^6,
+// summed over the three velocity components (sum over bins = mean |v|^2 over
+// the sample points). y: state [5][N][nc] of a cubic mesh of n^3 cells,
+// degree k. bins_out: host array of n_bins(M) doubles (the call synchronises
+// the stream). *cufft_status: 0, a cufftResult, or -1 if bytes is too small.
+cudaError_t velocity_spectrum(int k, const double* y, int n, int sub, void* work, size_t bytes, double* bins_out,
+                              cudaStream_t s, int* cufft_status);
+
+}  // namespace spec
+}  // namespace dg
