@@ -93,6 +93,7 @@ def _load():
                 "orc_totals": (None, [P, dp, dp]),
                 "orc_diagnostics": (None, [P, dp, dp]),
                 "orc_sample_velocity": (C.c_int, [P, dp, C.c_int, C.c_int, dp]),
+                "orc_sample_density": (C.c_int, [P, dp, C.c_int, dp]),
                 "orc_num_threads": (C.c_int, []),
             }
             for name, (res, args) in sig.items():
@@ -333,6 +334,28 @@ class Oracle:
         M = self.n[0] * sub
         out = np.zeros((M, M, M))
         assert self._call("orc_sample_velocity", _dp(_f64(w)), int(sub), int(comp), _dp(out)) == OK
+        return out
+
+    def sample_density(self, w, sub):
+        M = self.n[0] * sub
+        out = np.zeros((M, M, M))
+        assert self._call("orc_sample_density", _dp(_f64(w)), int(sub), _dp(out)) == OK
+        return out
+
+    def density_pdf(self, w, sub, lo, hi, nb):
+        """Sect. 4.4: counts of ln(rho) at the sub-cell centres in nb equal
+        bins of [lo, hi), plus the counts below lo (or rho not positive) and
+        at or above hi: array of nb + 2."""
+        r = self.sample_density(w, sub).ravel()
+        out = np.zeros(nb + 2, dtype=np.int64)
+        good = r > 0
+        out[0] += int(np.count_nonzero(~good))
+        sv = np.log(r[good])
+        out[0] += int(np.count_nonzero(sv < lo))
+        out[nb + 1] = int(np.count_nonzero(sv >= hi))
+        mid = sv[(sv >= lo) & (sv < hi)]
+        j = np.minimum(np.floor((mid - lo) / (hi - lo) * nb).astype(np.int64), nb - 1)
+        out[1:nb + 1] = np.bincount(j, minlength=nb)
         return out
 
     def velocity_spectrum(self, w, sub):

@@ -970,3 +970,22 @@ int orc_sample_velocity(const orc_params* p, const double* w, int sub, int comp,
       }
   return ORC_OK;
 }
+
+/* Sect. 4.4: the density field sampled below the cell size for PDFs. */
+int orc_sample_density(const orc_params* p, const double* w, int sub, double* out) {
+  if (check_params(p) || sub < 1) return ORC_ERR_ARG;
+  if (p->n[0] != p->n[1] || p->n[1] != p->n[2]) return ORC_ERR_ARG;
+  int n = p->n[0], M = n * sub;
+#pragma omp parallel for schedule(static)
+  for (long Z = 0; Z < M; ++Z)
+    for (long Y = 0; Y < M; ++Y)
+      for (long X = 0; X < M; ++X) {
+        double xi[3] = {-1.0 + (2.0 * (X % sub) + 1.0) / sub, -1.0 + (2.0 * (Y % sub) + 1.0) / sub,
+                        -1.0 + (2.0 * (Z % sub) + 1.0) / sub};
+        long cell = ((Z / sub) * n + Y / sub) * n + X / sub;
+        double U[5];
+        orc_eval(p, w, cell, xi, U);
+        out[(Z * M + Y) * M + X] = U[0];
+      }
+  return ORC_OK;
+}

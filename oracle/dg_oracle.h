@@ -125,6 +125,8 @@ void orc_diagnostics(const orc_params* p, const double* w, double* out3);
  * (Sect. 3.3 spectra sample the solution below the cell size): out [M][M][M]
  * with M = n sub, last index along x. */
 int orc_sample_velocity(const orc_params* p, const double* w, int sub, int comp, double* out);
+/* The density of the state polynomial on the same grid (Sect. 4.4 PDFs). */
+int orc_sample_density(const orc_params* p, const double* w, int sub, double* out);
 int orc_num_threads(void);
 
 #ifdef __cplusplus
