@@ -221,6 +221,15 @@ int dg_diagnostics(dg_ctx* ctx, double* out3);
 int dg_spectrum_sizes(const dg_ctx* ctx, int sub, size_t* work_bytes, int* n_bins);
 int dg_velocity_spectrum(dg_ctx* ctx, int sub, void* work_dev, size_t work_bytes, double* spectrum);
 
+/* Volume-weighted density PDF of the bound state (Sect. 4.4 density PDFs):
+ * counts of s = ln(rho) of the state polynomial at the centres of sub^3
+ * equal sub-cells of every cell (cubic mesh of a cubic box, 1 <= sub <= 8)
+ * in n_bins (1..4096) equal bins of [lo, hi): counts[1 + j] for
+ * floor((s - lo) / (hi - lo) n_bins) = j, counts[0] below lo (and samples
+ * whose density is not positive and finite), counts[n_bins + 1] at or above
+ * hi; host array of n_bins + 2 int64. Uses the bound scratch; synchronises. */
+int dg_density_pdf(dg_ctx* ctx, int sub, double lo, double hi, int n_bins, long long* counts);
+
 /* Synchronise the bound stream and report (and clear) the device error
  * word. */
 int dg_check(dg_ctx* ctx);

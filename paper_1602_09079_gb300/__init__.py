@@ -65,6 +65,7 @@ _SIGS = {
     "dg_diagnostics": (C.c_int, [C.c_void_p, C.c_void_p]),
     "dg_spectrum_sizes": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_size_t), C.POINTER(C.c_int)]),
     "dg_velocity_spectrum": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t, C.c_void_p]),
+    "dg_density_pdf": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_int, C.c_void_p]),
     "dg_check": (C.c_int, [C.c_void_p]),
     "dg_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
     "dg_kernel_stats": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -249,6 +250,13 @@ def dg_velocity_spectrum(ctx, sub, work, work_bytes, n_bins):
     out = np.zeros(n_bins)
     _check(load().dg_velocity_spectrum(ctx, int(sub), _ptr(work), int(work_bytes), out.ctypes.data),
            "dg_velocity_spectrum")
+    return out
+
+
+def dg_density_pdf(ctx, sub, lo, hi, n_bins):
+    out = np.zeros(n_bins + 2, dtype=np.int64)
+    _check(load().dg_density_pdf(ctx, int(sub), float(lo), float(hi), int(n_bins), out.ctypes.data),
+           "dg_density_pdf")
     return out
 
 
@@ -470,6 +478,11 @@ class Solver:
         nbytes, nb = dg_spectrum_sizes(self.ctx, sub)
         work = self.torch.empty(nbytes, dtype=self.torch.uint8, device=self.device)
         return dg_velocity_spectrum(self.ctx, sub, work, nbytes, nb)
+
+    def density_pdf(self, sub, lo, hi, n_bins):
+        """Counts of ln(rho) at sub^3 sub-cell centres per cell: [below lo,
+        n_bins bins of [lo, hi), at or above hi]."""
+        return dg_density_pdf(self.ctx, sub, lo, hi, n_bins)
 
     def diagnostics(self):
         """(rms Mach of the cell means, kinetic energy of the means,

@@ -905,6 +905,9 @@ int dg_diagnostics(dg_ctx* c, double* out3) {
 }
 
 namespace {
+// the PDF counts live in the partial-sum scratch (at least 2 kRedBlocks x 5 entries)
+constexpr int kMaxPdfBins = 4096;
+
 int spectrum_args(const dg_ctx* c, int sub, int* M) {
   if (!c || sub < 1 || sub > 8) return DG_ERR_ARG;
   const Geo& g = c->geo;
@@ -936,6 +939,18 @@ int dg_velocity_spectrum(dg_ctx* c, int sub, void* work_dev, size_t work_bytes, 
   DG_CUDA(dg::spec::velocity_spectrum(c->k, c->y, c->geo.nx, sub, work_dev, work_bytes, spectrum, c->stream, &cst));
   if (cst == -1) return DG_ERR_ARG;
   if (cst != 0) return DG_ERR_CUDA;
+  return DG_OK;
+}
+
+int dg_density_pdf(dg_ctx* c, int sub, double lo, double hi, int n_bins, long long* counts) {
+  DG_TRY(need_bound(c));
+  int M = 0;
+  DG_TRY(spectrum_args(c, sub, &M));
+  if (!counts || n_bins < 1 || n_bins > kMaxPdfBins || !(hi > lo) || !std::isfinite(lo) || !std::isfinite(hi))
+    return DG_ERR_ARG;
+  DG_TRY(set_device(c));
+  DG_CUDA(dg::spec::density_pdf(c->k, c->y, c->geo.nx, sub, lo, hi, n_bins,
+                                reinterpret_cast<unsigned long long*>(c->part), counts, c->stream));
   return DG_OK;
 }
 

@@ -91,7 +91,61 @@ cufftResult make_plan(int M, cufftHandle* plan, size_t* ws) {
   return r;
 }
 
+// histogram of ln(rho) of the state polynomial at the sub-cell centres:
+// counts[0] below lo (and non-positive or non-finite densities),
+// counts[1 + j] for floor((ln rho - lo) / (hi - lo) * nb) = j, counts[nb + 1]
+// at or above hi; integer counts (order-independent)
+__global__ void density_hist_kernel(const double* __restrict__ y, int k, int n, int sub, double lo, double hi, int nb,
+                                    unsigned long long* __restrict__ counts) {
+  extern __shared__ unsigned int shc[];
+  for (int b = threadIdx.x; b < nb + 2; b += blockDim.x) shc[b] = 0u;
+  __syncthreads();
+  const int N = nmodes(k), M = n * sub;
+  const long long total = (long long)M * M * M, nc = (long long)n * n * n;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int X = (int)(e % M), Y = (int)((e / M) % M), Z = (int)(e / ((long long)M * M));
+    const long long cell = ((long long)(Z / sub) * n + Y / sub) * n + X / sub;
+    const double xi[3] = {-1.0 + (2.0 * (X % sub) + 1.0) / sub, -1.0 + (2.0 * (Y % sub) + 1.0) / sub,
+                          -1.0 + (2.0 * (Z % sub) + 1.0) / sub};
+    double P[3][4];
+    for (int a = 0; a < 3; ++a)
+      for (int u = 0; u <= k; ++u) P[a][u] = scaled_legendre(u, xi[a]);
+    double rho = 0.0;
+    for (int l = 0; l < N; ++l) {
+      int u, v, w;
+      mode_uvw(l, u, v, w);
+      rho += y[(size_t)l * nc + cell] * (P[0][u] * P[1][v] * P[2][w]);
+    }
+    int b = 0;
+    if (rho > 0.0 && isfinite(rho)) {
+      const double sv = log(rho);
+      if (sv >= hi) {
+        b = nb + 1;
+      } else if (sv >= lo) {
+        const int j = (int)floor((sv - lo) / (hi - lo) * nb);
+        b = 1 + (j < nb ? j : nb - 1);
+      }
+    }
+    atomicAdd(&shc[b], 1u);
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < nb + 2; b += blockDim.x)
+    if (shc[b]) atomicAdd(&counts[b], (unsigned long long)shc[b]);
+}
+
 }  // namespace
+
+cudaError_t density_pdf(int k, const double* y, int n, int sub, double lo, double hi, int nb,
+                        unsigned long long* counts_dev, long long* counts_host, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(counts_dev, 0, sizeof(unsigned long long) * (nb + 2), s);
+  if (e != cudaSuccess) return e;
+  density_hist_kernel<<<1024, 256, sizeof(unsigned int) * (nb + 2), s>>>(y, k, n, sub, lo, hi, nb, counts_dev);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  e = cudaMemcpyAsync(counts_host, counts_dev, sizeof(unsigned long long) * (nb + 2), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(s);
+}
 
 int n_bins(int M) { return (int)std::floor(std::sqrt(3.0) * M / 2.0) + 2; }
 

@@ -24,5 +24,13 @@ size_t work_bytes(int M);
 cudaError_t velocity_spectrum(int k, const double* y, int n, int sub, void* work, size_t bytes, double* bins_out,
                               cudaStream_t s, int* cufft_status);
 
+// density PDF: counts of ln(rho) at the sub^3 sub-cell centres of every cell
+// in nb equal bins of [lo, hi), plus counts[0] (below lo, or rho not
+// positive/finite) and counts[nb + 1] (at or above hi). counts_dev: device
+// array of nb + 2 entries (cleared here); counts_host receives them
+// (synchronises the stream).
+cudaError_t density_pdf(int k, const double* y, int n, int sub, double lo, double hi, int nb,
+                        unsigned long long* counts_dev, long long* counts_host, cudaStream_t s);
+
 }  // namespace spec
 }  // namespace dg
