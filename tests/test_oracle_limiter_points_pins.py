@@ -80,3 +80,30 @@ def test_interior_dip_is_caught_only_by_the_union():
     assert fS[0] == 0 and np.array_equal(wS, w)
     assert fU[0] & 1
     assert abs(prim_min(oU, wU, 0, S + V)[0] - eps) <= 1e-12
+
+
+def test_face_minimum_gives_the_same_limit_for_both_sets():
+    """A linear density rho = 1 + a Pt1(x) takes its minimum at x = -1, a
+    GLL end point in S; the interior Gauss points lie above it. With the
+    floor above that minimum, theta1 over S and over the union coincide and
+    both limiters return the same state bit for bit (pressure stays far from
+    its floor at rest)."""
+    k, n = 2, (2, 1, 1)
+    probe = oracle.Oracle(n, k, G)
+    idx = {tuple(x): i for i, x in enumerate(oracle.mode_exponents(k))}
+    w = np.zeros(probe.state_shape)
+    w[..., 0, 0] = 1.0
+    w[..., 4, 0] = 50.0
+    w[..., 0, idx[(1, 0, 0)]] = 0.5  # minimum 1 - 0.5 sqrt(3) = 0.134 at x = -1
+    S, V = points(k)
+    rS, _ = prim_min(probe, w, 0, S)
+    rV, _ = prim_min(probe, w, 0, V)
+    assert abs(rS - (1 - 0.5 * np.sqrt(3))) <= 1e-14 and rV > rS + 0.05
+    eps = 0.2
+    oS = oracle.Oracle(n, k, G, eps_rho=eps, eps_p=1e-6)
+    oU = oracle.Oracle(n, k, G, limiter_points=oracle.LIMIT_S_VOLUME, eps_rho=eps, eps_p=1e-6)
+    stS, wS, fS, _ = oS.limit(w)
+    stU, wU, fU, _ = oU.limit(w)
+    assert stS == 0 and stU == 0
+    assert np.all(fS & 1) and np.array_equal(fS, fU) and np.array_equal(wS, wU)
+    assert abs(prim_min(oS, wS, 0, S + V)[0] - eps) <= 1e-12

@@ -44,3 +44,22 @@ def test_counts_of_a_random_state_add_up():
     assert c.sum() == (5 * sub) ** 3
     r = o.sample_density(w, sub)
     assert c[1:65].sum() == np.count_nonzero((np.log(r) >= -0.5) & (np.log(r) < 0.5))
+
+
+def test_non_positive_density_counts_below():
+    """rho = 1 + a Pt1(x) with a sqrt(3) / 2 = 1.299 (sub = 2 puts the
+    samples at x = +-1/2): half the samples have rho = -0.299, which has no
+    logarithm and is counted in the low end entry, the other half
+    rho = 2.299, counted in its own bin."""
+    n, k, sub, nb, lo, hi = (3, 3, 3), 1, 2, 16, -1.0, 1.0
+    o = oracle.Oracle(n, k, G)
+    idx = {tuple(x): i for i, x in enumerate(oracle.mode_exponents(k))}
+    w = uniform(o, 1.0)
+    w[..., 4, 0] = 5.0
+    w[..., 0, idx[(1, 0, 0)]] = 1.5
+    M3 = (3 * sub) ** 3
+    r = o.sample_density(w, sub)
+    assert np.allclose(np.sort(np.unique(np.round(r, 12))), [1 - 0.75 * math.sqrt(3), 1 + 0.75 * math.sqrt(3)])
+    c = o.density_pdf(w, sub, lo, hi, nb)
+    j = int(math.floor((math.log(1 + 0.75 * math.sqrt(3)) - lo) / (hi - lo) * nb))
+    assert c.sum() == M3 and c[0] == M3 // 2 and c[1 + j] == M3 // 2
