@@ -528,6 +528,10 @@ __device__ __forceinline__ void vol_f32_points(const float* sW, float* sF, float
       sS[(2 * PC + ql) * C + c] = U[0] * a[2];
       sS[(3 * PC + ql) * C + c] = U[1] * a[0] + U[2] * a[1] + U[3] * a[2];
     }
+    // without the driving-field loads the scheduler hoists the next points'
+    // shared loads over this one and spills (ptxas: 836 B per thread); a
+    // compiler memory barrier keeps one point live at a time
+    if (!FORCE) asm volatile("" ::: "memory");
   }
 }
 
