@@ -13,6 +13,9 @@ budget closes: total energy change = injected work - dissipated energy.
 
     python -m paper_1602_09079_gb300.turbulence --n 64 --order 3 --t-end 12 --out run.json
 
+With --spectrum-sub S the final state's velocity power spectrum and density
+PDF (Sect. 4.3-4.4) on S^3 samples per cell are added to the output.
+
 The driving amplitude is scaled once so that the box rms of the acceleration
 starts at M c / t_s (the paper rescales its amplitude until the target Mach
 number is reached); the reached rms Mach number is an output.
@@ -31,7 +34,7 @@ from .forcing import OUDriving, half_space_modes
 
 
 def run(n=64, order=3, gamma=1.01, t_end=12.0, mach=0.3, precision="mixed", seed=1234, courant=0.3,
-        record_every=0.1, max_steps=10_000_000):
+        record_every=0.1, max_steps=10_000_000, spectrum_sub=0, pdf_range=(-0.5, 0.5), pdf_bins=100):
     s = Solver((n, n, n), order, gamma, forcing=True)
     s.set_precision(DG_PREC_MIXED if precision == "mixed" else DG_PREC_FP64)
     rho0, p0 = 1.0, 1.0 / gamma
@@ -89,6 +92,16 @@ def run(n=64, order=3, gamma=1.01, t_end=12.0, mach=0.3, precision="mixed", seed
             next_record += record_every
     s.check()
     wall = time.perf_counter() - t_wall
+    analysis = {}
+    if spectrum_sub > 0:
+        # final state (Sect. 4.3-4.4): velocity power spectrum and volume-weighted
+        # PDF of ln(rho), both on spectrum_sub^3 samples per cell
+        analysis["velocity_spectrum"] = {"sub": spectrum_sub,
+                                         "shells": [float(x) for x in s.velocity_spectrum(spectrum_sub)]}
+        lo, hi = pdf_range
+        counts = s.density_pdf(spectrum_sub, lo, hi, pdf_bins)
+        analysis["density_pdf"] = {"sub": spectrum_sub, "lo": lo, "hi": hi, "bins": pdf_bins,
+                                   "counts": [int(x) for x in counts]}
     late = [r for r in series if r["t"] >= 0.5 * t_end]
     return {
         "config": {"n": n, "order": order, "gamma": gamma, "t_end": t_end, "target_mach": mach,
@@ -102,6 +115,7 @@ def run(n=64, order=3, gamma=1.01, t_end=12.0, mach=0.3, precision="mixed", seed
             "budget_residual": series[-1]["total_energy_change"] - (work - diss),
         },
         "series": series,
+        **analysis,
     }
 
 
@@ -116,9 +130,15 @@ def main():
     ap.add_argument("--seed", type=int, default=1234)
     ap.add_argument("--courant", type=float, default=0.3)
     ap.add_argument("--record-every", type=float, default=0.1)
+    ap.add_argument("--spectrum-sub", type=int, default=0,
+                    help="if > 0, record the final velocity spectrum and density PDF on sub^3 samples per cell")
+    ap.add_argument("--pdf-lo", type=float, default=-0.5)
+    ap.add_argument("--pdf-hi", type=float, default=0.5)
+    ap.add_argument("--pdf-bins", type=int, default=100)
     ap.add_argument("--out", default=None)
     a = ap.parse_args()
-    res = run(a.n, a.order, a.gamma, a.t_end, a.mach, a.precision, a.seed, a.courant, a.record_every)
+    res = run(a.n, a.order, a.gamma, a.t_end, a.mach, a.precision, a.seed, a.courant, a.record_every,
+              spectrum_sub=a.spectrum_sub, pdf_range=(a.pdf_lo, a.pdf_hi), pdf_bins=a.pdf_bins)
     txt = json.dumps(res)
     if a.out:
         with open(a.out, "w") as f:
