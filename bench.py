@@ -207,6 +207,29 @@ def roofline_entry(kind, achieved, peak, unit, bound, traffic=None):
             "frac": (achieved / peak) if peak else None, "traffic": traffic}
 
 
+def step_roofline(k, mixed, nc, ms_per_step, hbm_gbs, fp64_peak=1.25e12):
+    """Whole-step roofline: algorithmic HBM bytes of one step (CFL, three
+    stages of faces and volume, energy reset; roofline.step_bytes) over the
+    measured step time against the measured HBM bandwidth, and for the FP64
+    path also the algorithmic FP64 flops of its face and volume kernels
+    against the FP64 peak (that path's bound)."""
+    from paper_1602_09079_gb300 import roofline as rl
+    sec = ms_per_step * 1e-3
+    byts = rl.step_bytes(k, mixed) * nc
+    gbs = byts / sec / 1e9
+    out = {"bound": "hbm", "achieved": gbs, "peak": hbm_gbs, "unit": "GB/s",
+           "frac": gbs / hbm_gbs if hbm_gbs else None, "bytes_per_step": byts,
+           "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
+    if not mixed:
+        vol = rl.volume_sf_flops(k, True) if k >= 2 else rl.volume_flops(k, True)
+        flops = 3 * (rl.face_sf_flops(k) + vol) * nc
+        out.update({"bound": "alu", "achieved": flops / sec / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
+                    "frac": flops / sec / fp64_peak, "flops_per_step": flops, "hbm_gbs": gbs,
+                    "hbm_frac": gbs / hbm_gbs if hbm_gbs else None,
+                    "peak_source": "derived: FP64 1.25 TFLOP/s datasheet"})
+    return out
+
+
 def ncu_traffic():
     """DRAM bytes per cell per launch of the profiled kernels, from the ncu
     capture summarised in profiles/ncu_traffic.json (a smaller mesh of the
@@ -414,12 +437,16 @@ def run_ours(args):
             "data": "synthetic",
             "config": workload_config(args, head),
             "roofline": kernel_roofline(head, 4 if head == "mixed" else 8),
+            "step_roofline": step_roofline(k, head == "mixed", nc, r_mx["ms_max"] / args.steps, hbm),
+            "value_x5_variables": 5 * value,
             "fp64": {
                 "value": value64,
                 "unit": "DOF-updates/s",
                 "ms_per_step": r_64["ms_max"] / args.steps,
                 "dtype": "f64",
                 "roofline": kernel_roofline("fp64", 8) if "fp64" in results else None,
+                "step_roofline": (step_roofline(k, False, nc, r_64["ms_max"] / args.steps, hbm)
+                                  if "fp64" in results else None),
                 "clocks": r_64["clocks"],
                 "gpu_launches": sum(v[0] for v in r_64["launches"].values()),
             },

@@ -98,6 +98,38 @@ def volume_bytes(k, tsize, forcing, reads_y0=True, shadow=False):
     return b
 
 
+def reset_bytes(k, mixed):
+    """energy_reset_kernel: reads the four FP64 means and the other density
+    and momentum coefficients (FP32 shadow on the mixed path, FP64
+    otherwise) and the old energy mean; writes the N energy modes (FP64,
+    plus their FP32 shadow on the mixed path)."""
+    N = (k + 1) * (k + 2) * (k + 3) // 6
+    if mixed:
+        return 4 * 8 + 4 * (N - 1) * 4 + 8 + N * (8 + 4)
+    return 4 * N * 8 + 8 + N * 8
+
+
+def cfl_bytes():
+    """cfl_kernel: the five means of each cell."""
+    return 5 * 8
+
+
+def step_bytes(k, mixed, forcing=True):
+    """Algorithmic HBM bytes per cell of one benchmark step: the CFL
+    reduction, three stages of face fluxes and volume kernel, and the energy
+    reset. Mixed path: the face kernel reads the FP32 shadow and writes FP32
+    fluxes; the first stage's volume kernel skips y_0."""
+    N, Q, Q2, Q3 = _dims(k)
+    if mixed:
+        faces = 3 * (5 * N * 4 + 15 * Q2 * 4)
+        vol = (volume_bytes(k, 4, forcing, reads_y0=False, shadow=True)
+               + 2 * volume_bytes(k, 4, forcing, shadow=True))
+    else:
+        faces = 3 * face_bytes(k, 8)
+        vol = 3 * volume_bytes(k, 8, forcing)
+    return cfl_bytes() + faces + vol + reset_bytes(k, mixed)
+
+
 def step_flops(k, forcing):
     """Per cell per SSP-RK3 step (3 stages), both RHS kernels."""
     return 3 * (face_flops(k) + volume_flops(k, forcing))
