@@ -13,7 +13,9 @@ budget closes: total energy change = injected work - dissipated energy.
 
     python -m paper_1602_09079_gb300.turbulence --n 64 --order 3 --t-end 12 --out run.json
 
-With --spectrum-sub S the final state's velocity power spectrum and density
+--checkpoint F --checkpoint-every T writes the state, the OU amplitudes and
+the run's counters to F ("{steps}" in F keeps one file per checkpoint);
+--resume F continues such a run, bit for bit if F was taken before t_end. With --spectrum-sub S the final state's velocity power spectrum and density
 PDF (Sect. 4.3-4.4) on S^3 samples per cell are added to the output.
 
 The driving amplitude is scaled once so that the box rms of the acceleration
@@ -25,6 +27,7 @@ from __future__ import annotations
 import argparse
 import json
 import math
+import os
 import time
 
 import numpy as np
@@ -33,9 +36,40 @@ from . import DG_PREC_FP64, DG_PREC_MIXED, Solver
 from .forcing import OUDriving, half_space_modes
 
 
+def save_checkpoint(path, state, theta, meta):
+    """One .npz file: the canonical state [nz][ny][nx][5][N] (FP64), the OU
+    amplitudes theta and the run's counters and records as JSON (floats
+    round-trip exactly). Written to a temporary file first, then renamed."""
+    tmp = path + ".tmp.npz"
+    np.savez(tmp, state=np.asarray(state, dtype=np.float64), theta=np.asarray(theta, dtype=np.float64),
+             meta=np.array(json.dumps(meta)))
+    os.replace(tmp, path)
+
+
+def load_checkpoint(path):
+    with np.load(path) as f:
+        return f["state"].copy(), f["theta"].copy(), json.loads(str(f["meta"]))
+
+
+# run parameters a resumed run must share with the checkpointed one
+_RESUME_KEYS = ("n", "order", "gamma", "target_mach", "precision", "seed", "courant", "record_every")
+
+
 def run(n=64, order=3, gamma=1.01, t_end=12.0, mach=0.3, precision="mixed", seed=1234, courant=0.3,
-        record_every=0.1, max_steps=10_000_000, spectrum_sub=0, pdf_range=(-0.5, 0.5), pdf_bins=100):
-    s = Solver((n, n, n), order, gamma, forcing=True)
+        record_every=0.1, max_steps=10_000_000, spectrum_sub=0, pdf_range=(-0.5, 0.5), pdf_bins=100,
+        checkpoint=None, checkpoint_every=None, resume=None, solver=None):
+    """checkpoint: .npz path written every checkpoint_every time units and
+    when the run stops ("{steps}" in it is replaced by the step count, which
+    keeps one file per checkpoint); resume: a checkpoint to continue from
+    (same parameters; the OU draws come from the same seeded stream). A run
+    resumed from a checkpoint taken before t_end (periodic, or where
+    max_steps stopped the run) reproduces the uninterrupted run bit for bit;
+    a run that reached t_end ended on a step shortened to land there, so
+    extending it to a later t_end is a slightly different trajectory.
+    solver: the Solver class (a stand-in for tests of the driver's host
+    logic)."""
+    Solver_ = Solver if solver is None else solver
+    s = Solver_((n, n, n), order, gamma, forcing=True)
     s.set_precision(DG_PREC_MIXED if precision == "mixed" else DG_PREC_FP64)
     rho0, p0 = 1.0, 1.0 / gamma
     c = math.sqrt(gamma * p0 / rho0)
@@ -69,6 +103,29 @@ def run(n=64, order=3, gamma=1.01, t_end=12.0, mach=0.3, precision="mixed", seed
     P = s.diagnostics()[2]
     series = []
     next_record = 0.0
+    cfg = {"n": n, "order": order, "gamma": gamma, "target_mach": mach, "precision": precision, "seed": seed,
+           "courant": courant, "record_every": record_every}
+    if resume:
+        state, theta, meta = load_checkpoint(resume)
+        for key in _RESUME_KEYS:
+            if meta["config"][key] != cfg[key]:
+                raise ValueError(f"checkpoint {resume}: {key} = {meta['config'][key]!r}, run asks {cfg[key]!r}")
+        s.set_state(state)
+        drv.theta = theta
+        drv.n_updates = meta["drv_updates"]
+        k_upd, next_update = meta["k_upd"], meta["next_update"]
+        s.set_forcing(drv.nvec, drv.ahat())
+        E0, work, diss, P = meta["E0"], meta["work"], meta["diss"], meta["P"]
+        t, steps, next_record = meta["t"], meta["steps"], meta["next_record"]
+        series = [r for r in meta["series"] if not r.get("end_only")]
+
+    def write_checkpoint():
+        meta = {"config": cfg, "t": t, "steps": steps, "k_upd": k_upd, "next_update": next_update,
+                "drv_updates": drv.n_updates, "E0": E0, "work": work, "diss": diss, "P": P,
+                "next_record": next_record, "series": series}
+        save_checkpoint(checkpoint.format(steps=steps), s.get_state(), drv.theta, meta)
+
+    next_ckpt = t + checkpoint_every if (checkpoint and checkpoint_every) else math.inf
     t_wall = time.perf_counter()
     while t < t_end - 1e-12 and steps < max_steps:
         dt = min(s.cfl_dt(courant), t_end - t)
@@ -85,12 +142,21 @@ def run(n=64, order=3, gamma=1.01, t_end=12.0, mach=0.3, precision="mixed", seed
             s.set_forcing(drv.nvec, drv.ahat())
             next_update += dt_update
             P = s.diagnostics()[2]
-        if t >= next_record - 1e-12 or t >= t_end - 1e-12:
+        at_record = t >= next_record - 1e-12
+        if at_record or t >= t_end - 1e-12:
             d = s.diagnostics()
             series.append({"t": t, "steps": steps, "rms_mach": d[0], "kinetic": d[1], "power": d[2],
                            "injected": work, "dissipated": diss, "total_energy_change": s.totals()[4] - E0})
-            next_record += record_every
+            if at_record:
+                next_record += record_every
+            else:
+                series[-1]["end_only"] = True  # taken because the run ends here
+        if t >= next_ckpt - 1e-12:
+            write_checkpoint()
+            next_ckpt += checkpoint_every
     s.check()
+    if checkpoint:
+        write_checkpoint()
     wall = time.perf_counter() - t_wall
     analysis = {}
     if spectrum_sub > 0:
@@ -135,10 +201,14 @@ def main():
     ap.add_argument("--pdf-lo", type=float, default=-0.5)
     ap.add_argument("--pdf-hi", type=float, default=0.5)
     ap.add_argument("--pdf-bins", type=int, default=100)
+    ap.add_argument("--checkpoint", default=None, help=".npz file written every --checkpoint-every and at the end")
+    ap.add_argument("--checkpoint-every", type=float, default=None)
+    ap.add_argument("--resume", default=None, help="continue from this checkpoint (same run parameters)")
     ap.add_argument("--out", default=None)
     a = ap.parse_args()
     res = run(a.n, a.order, a.gamma, a.t_end, a.mach, a.precision, a.seed, a.courant, a.record_every,
-              spectrum_sub=a.spectrum_sub, pdf_range=(a.pdf_lo, a.pdf_hi), pdf_bins=a.pdf_bins)
+              spectrum_sub=a.spectrum_sub, pdf_range=(a.pdf_lo, a.pdf_hi), pdf_bins=a.pdf_bins,
+              checkpoint=a.checkpoint, checkpoint_every=a.checkpoint_every, resume=a.resume)
     txt = json.dumps(res)
     if a.out:
         with open(a.out, "w") as f:
