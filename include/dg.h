@@ -27,8 +27,10 @@
  *
  * Streams and errors: every call enqueues on the bound CUDA stream and
  * returns without synchronising, except the calls that return host values
- * (dg_cfl_dt, dg_totals, dg_limit with n_limited, dg_energy_reset with
- * dissipated, dg_get_state to host, dg_check), which synchronise the stream.
+ * (dg_cfl_dt, dg_totals, dg_diagnostics, dg_velocity_spectrum,
+ * dg_density_pdf, dg_limit with n_limited, dg_energy_reset with dissipated,
+ * dg_get_state to host, dg_indicator_capture, dg_limiter_counts,
+ * dg_kernel_stats, dg_check), which synchronise the stream.
  * Conditions found on the device (non-finite values, a cell mean below the
  * positivity floor, Newton non-convergence in the limiter) set a sticky
  * device error word that the next synchronising call reports and clears.
@@ -118,7 +120,8 @@ int dg_project(dg_ctx* ctx, const double* q_points_dev);
 int dg_project_range(dg_ctx* ctx, const double* q_points_dev, int64_t first, int64_t count);
 
 /* R(y) of Eq. dg:eqn:time: volume integral (Eq. dg:eqn:volume_int) plus
- * surface integral with the HLLC numerical flux (Eq. dg:eqn:surface_int),
+ * surface integral with the numerical flux set by dg_set_flux (HLLC by
+ * default; Eq. dg:eqn:surface_int),
  * divided by |K| (Eq. dg:eqn:time_deriv, orthonormal basis), plus the
  * driving source (Sect. 3.1) when set. y_dev and R_dev are device buffers in
  * the state layout; y_dev == NULL means the bound state. No limiting. Uses
@@ -147,14 +150,6 @@ int dg_cfl_dt(dg_ctx* ctx, double courant, double* dt_out);
 /* DG_PREC_FP64 or DG_PREC_MIXED. */
 int dg_set_precision(dg_ctx* ctx, int mode);
 
-/* Numerical flux of the surface integral (Sect. 2.3, Eq.
- * dg:eqn:surface_int, which allows an exact or an approximate HLLC Riemann
- * solver): DG_FLUX_HLLC (default; Einfeldt wave speeds) or DG_FLUX_EXACT
- * (Godunov flux of the exact Riemann solution, star pressure by Newton's
- * method, at most 50 iterations; a face point whose FP64 iteration does not
- * converge makes the next synchronising call return DG_ERR_NEWTON). Any
- * other value: DG_ERR_ARG. Applies to dg_rhs, dg_step and the indicator
- * capture from the next call on. */
 /* Point set of the positivity limiter (Sect. 2.5, which asks that it
  * contain every point where fluxes are evaluated): DG_LIMIT_S (default) is
  * S = S_x u S_y u S_z as the paper writes it, which covers the face
@@ -166,6 +161,14 @@ int dg_set_precision(dg_ctx* ctx, int mode);
 #define DG_LIMIT_S_VOLUME 1
 int dg_set_limiter_points(dg_ctx* ctx, int mode);
 
+/* Numerical flux of the surface integral (Sect. 2.3, Eq.
+ * dg:eqn:surface_int, which allows an exact or an approximate HLLC Riemann
+ * solver): DG_FLUX_HLLC (default; Einfeldt wave speeds) or DG_FLUX_EXACT
+ * (Godunov flux of the exact Riemann solution, star pressure by Newton's
+ * method, at most 50 iterations; a face point whose FP64 iteration does not
+ * converge makes the next synchronising call return DG_ERR_NEWTON). Any
+ * other value: DG_ERR_ARG. Applies to dg_rhs, dg_step and the indicator
+ * capture from the next call on. */
 #define DG_FLUX_HLLC 0
 #define DG_FLUX_EXACT 1
 int dg_set_flux(dg_ctx* ctx, int flux);
@@ -308,7 +311,8 @@ int dg_indicator_adam(float* params, float* m, float* v, const float* grads, int
                       float beta1, float beta2, float eps, int step, void* cuda_stream);
 
 /* ---- allocation-free entry point (no counterpart in the paper) ---------
- * R(y) exactly as dg_rhs computes it (same kernels; no driving source), for
+ * R(y) exactly as dg_rhs computes it (same kernels; HLLC flux, no driving
+ * source), for
  * callers that must not allocate device memory themselves: code whose device
  * memory is owned and budgeted by a host application or another framework's
  * allocator, where a cudaMalloc (or the implicit synchronisation of a
