@@ -194,7 +194,9 @@ def sample_cells(ncells, count, seed=7):
     rng = np.random.default_rng(seed)
     count = min(count, ncells)
     pick = rng.choice(ncells, size=count, replace=False)
-    pick[0] = 0
-    if count > 1:
-        pick[1] = ncells - 1
-    return np.unique(pick).astype(np.int64)
+    ends = ([0, ncells - 1] if ncells > 1 else [0])[:count]
+    out = np.unique(np.concatenate([ends, pick[len(ends):]]))
+    # an end cell that was also drawn leaves the sample short: top it up with
+    # the draws the end cells replaced (distinct from everything kept)
+    extra = [c for c in pick[:len(ends)] if c not in out][:count - len(out)]
+    return np.unique(np.concatenate([out, extra])).astype(np.int64)
