@@ -397,13 +397,18 @@ class Solver:
 
     # canonical <-> bound state
     def set_state(self, w):
+        """w: canonical-layout state, a host array or a CUDA tensor (moved to
+        this solver's device if it lives on another one)."""
         if hasattr(w, "data_ptr") and w.is_cuda:
-            w = w.contiguous().to(self.torch.float64)
+            w = w.to(device=self.device, dtype=self.torch.float64).contiguous()
+            if w.numel() != self.y.numel():
+                raise ValueError(f"state has {w.numel()} values, the mesh needs {self.y.numel()}")
             dg_set_state(self.ctx, w, 1)
-            self._keep = w
+            self._keep = w  # the copy is enqueued on the bound stream
         else:
             w = np.ascontiguousarray(w, dtype=np.float64)
-            assert w.size == self.y.numel()
+            if w.size != self.y.numel():
+                raise ValueError(f"state has {w.size} values, the mesh needs {self.y.numel()}")
             dg_set_state(self.ctx, w, 0)
 
     def get_state(self):
