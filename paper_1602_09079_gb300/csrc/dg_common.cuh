@@ -226,6 +226,12 @@ __device__ __forceinline__ void hllc_flux(int d, const T* UL, const T* UR, T gam
   }
   T aL = UL[0] * (SL - uL), aR = UR[0] * (SR - uR);
   T Ss = (pR - pL + uL * aL - uR * aR) / (aL - aR);
+  if constexpr (sizeof(T) == 4) {
+    // both FP32 pressures rounded to <= 0 (sound speeds clamped to zero) in
+    // a receding flow: S_L = u_L and S_R = u_R, so aL = aR = 0. Take S* = 0;
+    // the flux is then (0, p e_d, 0), the flux at a vacuum interface.
+    if (aL - aR == T(0)) Ss = T(0);
+  }
   const bool left = Ss >= T(0);
   const T* U = left ? UL : UR;
   const T* v = left ? vL : vR;
