@@ -1,0 +1,239 @@
+// driver.cpp -- runs the library's DG kernels (dg_kernels.cuh, degree DG_K)
+// under the host emulation of emu.h, launched with the grid, block and
+// shared-memory sizes of the library's launchers and in the order the C ABI
+// issues them (test infrastructure).
+//
+//   driver rhs  nx ny nz prec gamma in.bin out.bin
+//       R(y): face kernel, then the volume kernel in MODE_RHS (no driving)
+//   driver step nx ny nz prec gamma in.bin out.bin dt n_modes modes.bin c_iso rho0 lim_vol
+//       one dg_step (limiter of the input, three stages of face kernel,
+//       fused volume/stage kernel and queued limiter, with the driving field
+//       when n_modes > 0), then dg_energy_reset and the CFL reduction
+//
+//   driver hllc d gamma UL0..UL4 UR0..UR4
+//       the FP32 and FP64 HLLC fluxes of one face point
+//
+// prec: 0 FP64, 1 mixed. States in the state layout [5][N][n_cells], FP64.
+// Prints "err=<device error word> dissipated=<...> smax=<...>".
+#include <type_traits>
+
+#include "dg_kernels.cuh"
+using namespace dg;
+#include "tables.inc"
+
+constexpr int K = DG_K;
+using TB = Tab<K>;
+
+static unsigned grid1(long long n, int per) { return (unsigned)((n + per - 1) / per); }
+
+struct Setup {
+  std::vector<double> t64;
+  std::vector<float> t32;
+  Geo g{};
+  Ctrl ctrl{};
+  long long nc = 0;
+};
+
+// the tables as dg_init uploads them (device copies and constant banks)
+static void make_setup(Setup& S, int nx, int ny, int nz, double gamma, int lim_vol) {
+  S.t64.assign(TAB_STRIDE, 0.0);
+  build_tables<K>(S.t64.data());
+  S.t32.resize(TAB_STRIDE);
+  for (int i = 0; i < TAB_STRIDE; ++i) S.t32[i] = (float)S.t64[i];
+  for (int i = 0; i < TB::SIZE; ++i) c_tab32[i] = S.t32[i];
+  constexpr int KQ = (K + 1) * (K + 1), NSF = 3 * KQ + 2 * (K + 1);
+  for (int i = 0; i < KQ; ++i) {
+    c_sf64[i] = S.t64[TB::P1 + i];
+    c_sf64[KQ + i] = S.t64[TB::P1W + i];
+    c_sf64[2 * KQ + i] = S.t64[TB::D1W + i];
+  }
+  for (int i = 0; i < 2 * (K + 1); ++i) c_sf64[3 * KQ + i] = S.t64[TB::FEND + i];
+  for (int i = 0; i < NSF; ++i) c_sf32[i] = (float)c_sf64[i];
+  S.nc = (long long)nx * ny * nz;
+  Geo& g = S.g;
+  g.nx = nx;
+  g.ny = ny;
+  g.nz = nz;
+  g.nc = S.nc;
+  const int n3[3] = {nx, ny, nz};
+  for (int a = 0; a < 3; ++a) {
+    g.dx[a] = 1.0 / n3[a];
+    g.inv_dx[a] = 1.0 / g.dx[a];
+  }
+  g.gamma = gamma;
+  g.eps_rho = 1e-12;
+  g.eps_p = 1e-12;
+  g.lim_vol = lim_vol;
+}
+
+// face fluxes of the state ys (FP32 path: of its shadow yf)
+template <typename T>
+static void faces(Setup& S, const double* ys, float* yf, T* fh) {
+  if constexpr (sizeof(T) == 4)
+    emu::launch(grid1(S.nc, 32), 96, 0, [&] { face_flux_f32_kernel<K, 0>(yf, fh, S.g, &S.ctrl); });
+  else
+    emu::launch(grid1(S.nc, 32), FaceSF64<K>::THREADS, FaceSF64<K>::smem(),
+                [&] { face_sf64_kernel<K, 0>(ys, fh, S.g, &S.ctrl); });
+}
+
+// the volume kernel the launchers pick for (T, K) in MODE
+template <typename T, int MODE, bool FORCE>
+static void volume(Setup& S, const double* ys, float* yf, const T* fh, const T* field, StageArgs st, double* R) {
+  const long long nc = S.nc;
+  if constexpr (sizeof(T) == 4 && K <= 2) {
+    using CF = VolF32<K>;
+    emu::launch(grid1(nc, CF::C), CF::THREADS, CF::smem(FORCE), [&] {
+      volume_f32_kernel<K, MODE, FORCE>(yf, fh, field, S.t64.data(), S.g, st, R, &S.ctrl);
+    });
+  } else if constexpr (sizeof(T) == 4) {
+    using CF = VolSF<K, float>;
+    emu::launch(grid1(nc, CF::C), kThreads, CF::smem(), [&] {
+      volume_sfb_kernel<K, float, MODE, FORCE>(ys, yf, fh, field, S.t32.data(), S.t64.data(), S.g, st, R, &S.ctrl);
+    });
+  } else if constexpr (K >= 2) {
+    using CF = VolSF<K, double>;
+    emu::launch(grid1(nc, CF::C), kThreads, CF::smem(), [&] {
+      volume_sf_kernel<K, double, MODE, FORCE>(ys, nullptr, fh, field, S.t64.data(), S.t64.data(), S.g, st, R,
+                                               &S.ctrl);
+    });
+  } else {
+    using CF = VolCfg<K, double>;
+    emu::launch(grid1(nc, CF::C), kThreads, CF::smem(FORCE), [&] {
+      volume_kernel<K, double, MODE, FORCE>(ys, fh, field, S.t64.data(), S.t64.data(), S.g, st, R, &S.ctrl);
+    });
+  }
+}
+
+template <typename T>
+static void run_rhs(Setup& S, std::vector<double>& y, std::vector<double>& R) {
+  std::vector<float> yf(sizeof(T) == 4 ? y.size() : 1);
+  if (sizeof(T) == 4)
+    for (size_t i = 0; i < y.size(); ++i) yf[i] = (float)y[i];  // the library's shadow: round to nearest
+  std::vector<T> fh((size_t)15 * TB::Q2 * S.nc, T(std::nan("")));
+  faces<T>(S, y.data(), yf.data(), fh.data());
+  StageArgs st{};
+  volume<T, MODE_RHS, false>(S, y.data(), sizeof(T) == 4 ? yf.data() : nullptr, fh.data(), nullptr, st, R.data());
+  std::printf("err=%u dissipated=0 smax=0\n", S.ctrl.err);
+}
+
+template <typename T>
+static void run_step(Setup& S, std::vector<double>& y, double dt, const std::vector<double>& modes, int nm,
+                     double c_iso, double rho0) {
+  const long long nc = S.nc;
+  const bool force = nm > 0;
+  std::vector<T> field(force ? (size_t)3 * TB::Q3 * nc : 1, T(std::nan("")));
+  if (force)
+    emu::launch2(grid1(nc, kThreads), TB::Q3, kThreads, 0, [&] {
+      forcing_field_kernel<K, T>(field.data(), modes.data(), nm, S.t64.data(), S.g, 1.0, 1.0, 1.0);
+    });
+  const T* fld = force ? field.data() : nullptr;
+  emu::launch(grid1(nc, kThreads), kThreads, 0,
+              [&] { limit_kernel<K>(y.data(), nullptr, S.t64.data(), S.g, &S.ctrl); });
+  const bool shadow = sizeof(T) == 4;
+  std::vector<float> yf(shadow ? y.size() : 1);
+  if (shadow)
+    for (size_t i = 0; i < y.size(); ++i) yf[i] = (float)y[i];
+  float* yfp = shadow ? yf.data() : nullptr;
+  std::vector<T> fh((size_t)15 * TB::Q2 * nc, T(std::nan("")));
+  std::vector<double> ybuf(y.size(), std::nan(""));
+  std::vector<int> list(nc, -1);
+  const double a0[3] = {0.0, 0.75, 1.0 / 3.0}, b0[3] = {1.0, 0.25, 2.0 / 3.0};
+  const double* ys = y.data();
+  for (int s = 0; s < 3; ++s) {
+    double* out = s < 2 ? ybuf.data() : y.data();
+    faces<T>(S, ys, yfp, fh.data());
+    S.ctrl.n_flag = 0;
+    StageArgs st{ys, y.data(), out, a0[s], b0[s], dt, list.data(), yfp};
+    if (force) volume<T, MODE_STAGE, true>(S, ys, yfp, fh.data(), fld, st, nullptr);
+    else volume<T, MODE_STAGE, false>(S, ys, yfp, fh.data(), fld, st, nullptr);
+    emu::launch(152, kThreads, 0, [&] {
+      limit_list_kernel<K>(out, list.data(), &S.ctrl.n_flag, S.t64.data(), S.g, &S.ctrl, 1, yfp);
+    });
+    ys = out;
+  }
+  // energy reset (the shadow stays current on the mixed path) and its limiter
+  S.ctrl.n_flag = 0;
+  const unsigned nbr = grid1(nc, 32);
+  std::vector<double> part(nbr, 0.0);
+  ResetConsts<T> rc;
+  rc.c2g = (T)(c_iso * c_iso / (S.g.gamma - 1.0));
+  rc.inv_rho0 = (T)(1.0 / rho0);
+  rc.gm1 = (T)(S.g.gamma - 1.0);
+  rc.two_thirds = std::fabs(S.g.gamma - 1.0 - 2.0 / 3.0) < 1e-15 ? 1 : 0;
+  const T* tabT = sizeof(T) == 8 ? (const T*)(const void*)S.t64.data() : (const T*)(const void*)S.t32.data();
+  emu::launch(nbr, kThreads, 0, [&] {
+    energy_reset_kernel<K, T, 32>(y.data(), tabT, S.t64.data(), S.g, rc, part.data(), list.data(), &S.ctrl, yfp);
+  });
+  emu::launch(152, kThreads, 0, [&] {
+    limit_list_kernel<K>(y.data(), list.data(), &S.ctrl.n_flag, S.t64.data(), S.g, &S.ctrl, 0, yfp);
+  });
+  double diss = 0.0;
+  for (unsigned b = 0; b < nbr; ++b) diss += part[b];
+  diss *= S.g.dx[0] * S.g.dx[1] * S.g.dx[2];
+  unsigned nb = grid1(nc, kThreads);
+  if (nb > 152u * 8u) nb = 152u * 8u;
+  S.ctrl.cfl_max_bits = 0;
+  emu::launch(nb, kThreads, 0, [&] { cfl_kernel<K>(y.data(), S.g, &S.ctrl); });
+  double smax;
+  std::memcpy(&smax, &S.ctrl.cfl_max_bits, 8);
+  std::printf("err=%u dissipated=%.17g smax=%.17g\n", S.ctrl.err, diss, smax);
+}
+
+static bool read_file(const char* path, double* p, size_t n) {
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return false;
+  const bool ok = std::fread(p, 8, n, f) == n;
+  std::fclose(f);
+  return ok;
+}
+
+// driver hllc d gamma UL0..UL4 UR0..UR4: the FP32 and FP64 HLLC fluxes
+static int run_hllc(int argc, char** argv) {
+  if (argc != 14) return 2;
+  const int d = std::atoi(argv[2]);
+  const double gamma = std::atof(argv[3]);
+  float UL[5], UR[5], F[5];
+  double ULd[5], URd[5], Fd[5];
+  for (int i = 0; i < 5; ++i) {
+    ULd[i] = std::atof(argv[4 + i]);
+    URd[i] = std::atof(argv[9 + i]);
+    UL[i] = (float)ULd[i];
+    UR[i] = (float)URd[i];
+  }
+  hllc_flux<float>(d, UL, UR, (float)gamma, F);
+  hllc_flux<double>(d, ULd, URd, gamma, Fd);
+  std::printf("f32=%.9g,%.9g,%.9g,%.9g,%.9g f64=%.17g,%.17g,%.17g,%.17g,%.17g\n", F[0], F[1], F[2], F[3], F[4],
+              Fd[0], Fd[1], Fd[2], Fd[3], Fd[4]);
+  return 0;
+}
+
+int main(int argc, char** argv) {
+  if (argc >= 2 && std::strcmp(argv[1], "hllc") == 0) return run_hllc(argc, argv);
+  if (argc < 9) return 2;
+  const bool step = std::strcmp(argv[1], "step") == 0;
+  if (step ? argc != 15 : argc != 9) return 2;
+  const int nx = std::atoi(argv[2]), ny = std::atoi(argv[3]), nz = std::atoi(argv[4]), prec = std::atoi(argv[5]);
+  const double gamma = std::atof(argv[6]);
+  Setup S;
+  make_setup(S, nx, ny, nz, gamma, step ? std::atoi(argv[14]) : 0);
+  std::vector<double> y((size_t)5 * TB::N * S.nc);
+  if (!read_file(argv[7], y.data(), y.size())) return 3;
+  if (step) {
+    const double dt = std::atof(argv[9]), c_iso = std::atof(argv[12]), rho0 = std::atof(argv[13]);
+    const int nm = std::atoi(argv[10]);
+    std::vector<double> modes((size_t)9 * nm + 1);
+    if (nm > 0 && !read_file(argv[11], modes.data(), (size_t)9 * nm)) return 3;
+    if (prec) run_step<float>(S, y, dt, modes, nm, c_iso, rho0);
+    else run_step<double>(S, y, dt, modes, nm, c_iso, rho0);
+  } else {
+    std::vector<double> R(y.size(), 0.0);
+    if (prec) run_rhs<float>(S, y, R);
+    else run_rhs<double>(S, y, R);
+    y.swap(R);
+  }
+  FILE* f = std::fopen(argv[8], "wb");
+  if (!f) return 3;
+  std::fwrite(y.data(), 8, y.size(), f);
+  std::fclose(f);
+  return 0;
+}

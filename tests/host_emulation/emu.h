@@ -1,0 +1,160 @@
+// emu.h -- host emulation of the CUDA thread model, so that the DG kernels
+// can be compiled by g++ under AddressSanitizer / UndefinedBehaviorSanitizer
+// / ThreadSanitizer (test infrastructure: checks the kernels' memory accesses
+// and shared-memory synchronisation on the CPU; the library never runs on
+// the host). Blocks run one after another on one pool of OS threads, one per
+// CUDA thread; __syncthreads is a std::barrier of the block, a warp shuffle
+// exchanges through a per-warp barrier, __shared__ variables become static
+// (one block at a time), atomics are GCC atomic builtins, and the dynamic
+// shared memory is a per-block buffer poisoned with 0xCD.
+#pragma once
+#include <algorithm>
+#include <atomic>
+#include <barrier>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <functional>
+#include <memory>
+#include <thread>
+#include <vector>
+
+#define __global__
+#define __device__
+#define __host__
+#define __forceinline__ inline
+#define __launch_bounds__(...)
+#define __align__(n) alignas(n)
+#define __constant__
+#define __shared__ static
+
+struct emu_uint3 { unsigned x = 0, y = 0, z = 0; };
+
+namespace emu {
+struct Block {
+  std::unique_ptr<std::barrier<>> bar;
+  std::vector<std::unique_ptr<std::barrier<>>> warp;
+  std::vector<unsigned char> smem;
+  std::vector<uint64_t> shfl;
+};
+inline emu_uint3 g_blockIdx, g_blockDim, g_gridDim;
+inline thread_local emu_uint3 t_threadIdx;
+inline Block* g_block = nullptr;
+inline unsigned char* dyn_smem() { return g_block->smem.data(); }
+
+// run f() as grid x block threads (1D), dynamic shared memory of smem bytes
+template <class F>
+void launch2(unsigned grid, unsigned gridy, unsigned block, size_t smem, F&& f) {
+  g_gridDim = {grid, gridy, 1};
+  g_blockDim = {block, 1, 1};
+  const unsigned nblocks = grid * gridy, nw = (block + 31) / 32;
+  // one pool of `block` threads walks the blocks; the main thread sets each
+  // block up (fresh barriers, poisoned shared memory) between two pool-wide
+  // barriers
+  std::barrier<> start(block + 1), done(block + 1);
+  Block B;
+  auto setup = [&](unsigned bb) {
+    g_blockIdx = {bb % grid, bb / grid, 0};
+    B.bar = std::make_unique<std::barrier<>>(block);
+    B.warp.clear();
+    for (unsigned w = 0; w < nw; ++w)
+      B.warp.push_back(std::make_unique<std::barrier<>>(std::min(32u, block - 32 * w)));
+    B.smem.assign(smem + 16, 0xCD);  // poison: reads before writes show up
+    B.shfl.assign(block, 0);
+    g_block = &B;
+  };
+  std::vector<std::thread> th;
+  th.reserve(block);
+  for (unsigned t = 0; t < block; ++t)
+    th.emplace_back([&, t] {
+      t_threadIdx = {t, 0, 0};
+      for (unsigned bb = 0; bb < nblocks; ++bb) {
+        start.arrive_and_wait();
+        f();
+        B.bar->arrive_and_drop();
+        B.warp[t / 32]->arrive_and_drop();
+        done.arrive_and_wait();
+      }
+    });
+  for (unsigned bb = 0; bb < nblocks; ++bb) {
+    setup(bb);
+    start.arrive_and_wait();
+    done.arrive_and_wait();
+  }
+  for (auto& x : th) x.join();
+  g_block = nullptr;
+}
+template <class F>
+void launch(unsigned grid, unsigned block, size_t smem, F&& f) {
+  launch2(grid, 1, block, smem, f);
+}
+}  // namespace emu
+
+#define threadIdx (emu::t_threadIdx)
+#define blockIdx (emu::g_blockIdx)
+#define blockDim (emu::g_blockDim)
+#define gridDim (emu::g_gridDim)
+
+inline void __syncthreads() { emu::g_block->bar->arrive_and_wait(); }
+
+template <class T>
+inline T __shfl_xor_sync(unsigned, T v, int m) {
+  const unsigned t = threadIdx.x, w = t / 32, lane = t % 32;
+  auto& B = *emu::g_block;
+  uint64_t bits = 0;
+  std::memcpy(&bits, &v, sizeof(T));
+  B.shfl[t] = bits;
+  B.warp[w]->arrive_and_wait();
+  const uint64_t o = B.shfl[w * 32 + (lane ^ (unsigned)m)];
+  B.warp[w]->arrive_and_wait();
+  T r;
+  std::memcpy(&r, &o, sizeof(T));
+  return r;
+}
+
+template <class T> inline T __ldg(const T* p) { return *p; }
+template <class T> inline T __ldcg(const T* p) { return *p; }
+
+inline unsigned atomicAdd(unsigned* p, unsigned v) { return __atomic_fetch_add(p, v, __ATOMIC_SEQ_CST); }
+inline int atomicAdd(int* p, int v) { return __atomic_fetch_add(p, v, __ATOMIC_SEQ_CST); }
+inline unsigned long long atomicAdd(unsigned long long* p, unsigned long long v) {
+  return __atomic_fetch_add(p, v, __ATOMIC_SEQ_CST);
+}
+inline double atomicAdd(double* p, double v) {
+  double old = __atomic_load_n((long long*)p, __ATOMIC_SEQ_CST), nw;
+  long long ob, nb;
+  do {
+    std::memcpy(&ob, p, 8);
+    std::memcpy(&old, &ob, 8);
+    nw = old + v;
+    std::memcpy(&nb, &nw, 8);
+  } while (!__atomic_compare_exchange_n((long long*)p, &ob, nb, false, __ATOMIC_SEQ_CST, __ATOMIC_SEQ_CST));
+  return old;
+}
+inline unsigned atomicOr(unsigned* p, unsigned v) { return __atomic_fetch_or(p, v, __ATOMIC_SEQ_CST); }
+inline unsigned long long atomicMax(unsigned long long* p, unsigned long long v) {
+  unsigned long long o = __atomic_load_n(p, __ATOMIC_SEQ_CST);
+  while (o < v && !__atomic_compare_exchange_n(p, &o, v, false, __ATOMIC_SEQ_CST, __ATOMIC_SEQ_CST)) {
+  }
+  return o;
+}
+
+inline long long __double_as_longlong(double x) { long long r; std::memcpy(&r, &x, 8); return r; }
+inline double __longlong_as_double(long long x) { double r; std::memcpy(&r, &x, 8); return r; }
+inline unsigned __float_as_uint(float x) { unsigned r; std::memcpy(&r, &x, 4); return r; }
+inline float __uint_as_float(unsigned x) { float r; std::memcpy(&r, &x, 4); return r; }
+inline int __double2hiint(double x) { return (int)(unsigned)((unsigned long long)__double_as_longlong(x) >> 32); }
+inline int __double2loint(double x) { return (int)(unsigned)((unsigned long long)__double_as_longlong(x) & 0xffffffffull); }
+inline double __hiloint2double(int hi, int lo) {
+  return __longlong_as_double((long long)(((unsigned long long)(unsigned)hi << 32) | (unsigned)lo));
+}
+inline double rsqrt(double x) { return 1.0 / std::sqrt(x); }
+inline float rsqrtf(float x) { return 1.0f / std::sqrt(x); }
+using std::cbrt;
+using std::fmax;
+using std::fmin;
+using std::isfinite;
+using std::pow;
+using std::sqrt;

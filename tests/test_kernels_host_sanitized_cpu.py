@@ -1,0 +1,195 @@
+"""Memory safety of the DG kernels, checked on the CPU: the role
+compute-sanitizer plays on a GPU, with the kernel sources compiled by g++
+under AddressSanitizer and UndefinedBehaviorSanitizer in a host emulation of
+the CUDA thread model (tests/host_emulation: one OS thread per CUDA thread,
+barriers for __syncthreads and warp shuffles, shared memory poisoned). Every
+global, shared and table access of the face, volume, stage, limiter, energy
+reset, forcing-field and CFL kernels is bounds-checked on meshes whose cell
+count leaves ragged tiles, at every degree and in both precisions, with the
+launch sizes of the library's launchers and in the order the C ABI issues
+the kernels. The results are compared with the oracle only to confirm that
+the emulation ran the kernels' arithmetic; parity of the GPU path itself is
+what the -m gpu tests check."""
+import concurrent.futures as cf
+import os
+import shutil
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle
+import synthetic as syn
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_1602_09079_gb300", "csrc")
+EMU = os.path.join(ROOT, "tests", "host_emulation")
+FLAGS = ["-std=c++20", "-O1", "-g", "-pthread", "-fsanitize=address,undefined", "-fno-sanitize-recover=undefined",
+         "-fno-omit-frame-pointer"]
+
+
+def _generate(dst):
+    """The kernel headers with the dynamic shared memory taken from the
+    emulated block's buffer, and the table builder of dg_api.cu."""
+    for f in ("dg_common.cuh", "dg_kernels.cuh"):
+        s = open(os.path.join(CSRC, f)).read()
+        s = s.replace("extern __shared__ __align__(16) unsigned char smem_raw[];",
+                      "unsigned char* smem_raw = emu::dyn_smem();")
+        assert "extern __shared__" not in s, f
+        open(os.path.join(dst, f), "w").write(s)
+    api = open(os.path.join(CSRC, "dg_api.cu")).read()
+    a = api.index("// ----------------------------------------------------------------- tables")
+    b = api.index("Launchers launchers_for(int k)")
+    open(os.path.join(dst, "tables.inc"), "w").write(api[a:b] + "}  // namespace\n")
+
+
+@pytest.fixture(scope="module")
+def drivers():
+    if shutil.which("g++") is None:
+        pytest.skip("g++ not available")
+    d = tempfile.mkdtemp(prefix="dg_host_emu_")
+    _generate(d)
+
+    def build(k):
+        exe = os.path.join(d, f"driver_k{k}")
+        cmd = ["g++", *FLAGS, "-I", EMU, "-I", d, "-include", os.path.join(EMU, "emu.h"), f"-DDG_K={k}",
+               os.path.join(EMU, "driver.cpp"), "-o", exe]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr[-4000:]
+        return exe
+
+    with cf.ThreadPoolExecutor(4) as ex:
+        exes = list(ex.map(build, range(4)))
+    yield d, exes
+    shutil.rmtree(d, ignore_errors=True)
+
+
+def _layout(w):
+    nc = w.shape[0] * w.shape[1] * w.shape[2]
+    return np.ascontiguousarray(w.reshape(nc, 5, w.shape[-1]).transpose(1, 2, 0))
+
+
+def _canonical(y, shape):
+    nc = shape[0] * shape[1] * shape[2]
+    return y.reshape(5, shape[-1], nc).transpose(2, 0, 1).reshape(shape)
+
+
+def _run(exe, args, d):
+    r = subprocess.run([exe, *map(str, args)], capture_output=True, text=True, timeout=900, cwd=d)
+    assert r.returncode == 0, (r.returncode, r.stderr[-4000:])
+    return dict(kv.split("=") for kv in r.stdout.split())
+
+
+def normwise(a, b):
+    return max(np.max(np.abs(a[..., i, :] - b[..., i, :])) / np.max(np.abs(b[..., i, :])) for i in range(5))
+
+
+N_MESH = (5, 3, 7)  # 105 cells: ragged tiles of 8, 32 and 256 cells
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("k", [0, 1, 2, 3])
+def test_rhs_kernels_clean(drivers, k, prec):
+    d, exes = drivers
+    g = syn.GAMMA
+    w = syn.random_state(N_MESH, oracle.nmodes(k), g, seed=40 + k, high=0.01)
+    fin, fout = os.path.join(d, f"r{k}{prec}.in"), os.path.join(d, f"r{k}{prec}.out")
+    _layout(w).tofile(fin)
+    info = _run(exes[k], ["rhs", *N_MESH, prec, repr(g), fin, fout], d)
+    assert info["err"] == "0"
+    R = _canonical(np.fromfile(fout), w.shape)
+    assert normwise(R, oracle.Oracle(N_MESH, k, g).rhs(w)) <= (1e-12 if prec == 0 else 2e-5)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("k", [0, 1, 2, 3])
+def test_step_kernels_clean(drivers, k, prec):
+    """A driven step whose high modes are large enough for the limiter to
+    act in every stage (queued cells, theta1 and theta2), then the energy
+    reset and the CFL reduction; against the oracle's step and reset (FP64
+    to 1e-9: the pressure Newton iteration near the 1e-12 floor is
+    ill-conditioned, mixed to 1e-5)."""
+    d, exes = drivers
+    g = syn.GAMMA
+    n = N_MESH
+    w = syn.random_state(n, oracle.nmodes(k), g, seed=50 + k, high=0.3)
+    nv = syn.driving_modes(1.0, 2.0)
+    ah = np.random.default_rng(60 + k).normal(size=(len(nv), 6)) * 0.5
+    o = oracle.Oracle(n, k, g)
+    o.set_forcing(nv, ah)
+    st, dt = o.cfl_dt(w, 0.3)
+    assert st == 0
+    st, w1 = o.step(w, dt)
+    assert st == 0
+    st, w2, dref = o.energy_reset(w1, 0.7, 1.0)
+    assert st == 0
+    fin, fout, fm = (os.path.join(d, f"s{k}{prec}.{x}") for x in ("in", "out", "modes"))
+    _layout(w).tofile(fin)
+    np.ascontiguousarray(np.concatenate([nv.astype(np.float64), ah], axis=1)).tofile(fm)
+    info = _run(exes[k], ["step", *n, prec, repr(g), fin, fout, repr(dt), len(nv), fm, 0.7, 1.0, 0], d)
+    assert info["err"] == "0"
+    y = _canonical(np.fromfile(fout), w.shape)
+    assert normwise(y, w2) <= (1e-9 if prec == 0 else 1e-5)
+    assert abs(float(info["dissipated"]) - dref) <= (1e-9 if prec == 0 else 1e-5) * abs(dref)
+    # the CFL reduction saw the reset state
+    assert float(info["smax"]) > 0
+
+
+def test_step_with_volume_limiter_points_clean(drivers):
+    d, exes = drivers
+    g, k, n = syn.GAMMA, 2, N_MESH
+    w = syn.random_state(n, oracle.nmodes(k), g, seed=70, high=0.3)
+    o = oracle.Oracle(n, k, g, limiter_points=oracle.LIMIT_S_VOLUME)
+    st, dt = o.cfl_dt(w, 0.3)
+    st, w1 = o.step(w, dt)
+    assert st == 0
+    st, w2, dref = o.energy_reset(w1, 0.7, 1.0)
+    fin, fout = os.path.join(d, "v.in"), os.path.join(d, "v.out")
+    _layout(w).tofile(fin)
+    info = _run(exes[k], ["step", *n, 1, repr(g), fin, fout, repr(dt), 0, fin, 0.7, 1.0, 1], d)
+    assert info["err"] == "0"
+    assert normwise(_canonical(np.fromfile(fout), w.shape), w2) <= 1e-5
+
+
+def _hllc(exe, d, g, UL, UR, tmp):
+    info = _run(exe, ["hllc", d, repr(g), *(repr(float(x)) for x in UL), *(repr(float(x)) for x in UR)], tmp)
+    return (np.array([float(x) for x in info["f32"].split(",")]),
+            np.array([float(x) for x in info["f64"].split(",")]))
+
+
+def _cons(rho, v, p, g):
+    return [rho, rho * v[0], rho * v[1], rho * v[2], p / (g - 1) + 0.5 * rho * (v[0] ** 2 + v[1] ** 2 + v[2] ** 2)]
+
+
+def test_fp32_hllc_receding_vacuum_states(drivers):
+    """FP32 traces of a state limited in FP64 can round both face pressures
+    to <= 0; the sound speeds are then clamped to zero, and in a receding
+    flow (u_L < 0 < u_R) both HLLC wave speeds equal the fluid velocities,
+    so the contact-speed denominator vanishes. The flux must stay finite:
+    (0, p_L e_d, 0), the flux at a vacuum interface. Away from that case
+    the FP32 flux equals the FP64 one to FP32 rounding."""
+    d, exes = drivers
+    g = syn.GAMMA
+    for dirn in range(3):
+        vL, vR = np.zeros(3), np.zeros(3)
+        vL[dirn], vR[dirn] = -0.24, 0.12
+        vL[(dirn + 1) % 3] = 0.07
+        pL = -1e-4  # pressures below zero, as FP32 rounding can leave them
+        UL = _cons(0.9989, vL, pL, g)
+        UR = _cons(0.9451, vR, -3e-4, g)
+        f32, _ = _hllc(exes[2], dirn, g, UL, UR, d)
+        assert np.all(np.isfinite(f32)), f32
+        expect = np.zeros(5)
+        expect[1 + dirn] = pL
+        assert np.max(np.abs(f32 - expect)) <= 1e-7, f32
+        # and the mirrored pair (the contact speed from the other side)
+        f32m, _ = _hllc(exes[2], dirn, g, UR, UL, d)
+        assert np.all(np.isfinite(f32m))
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        dirn = int(rng.integers(3))
+        UL = _cons(rng.uniform(0.5, 2), rng.uniform(-1, 1, 3), rng.uniform(0.2, 2), g)
+        UR = _cons(rng.uniform(0.5, 2), rng.uniform(-1, 1, 3), rng.uniform(0.2, 2), g)
+        f32, f64 = _hllc(exes[2], dirn, g, UL, UR, d)
+        assert np.max(np.abs(f32 - f64)) <= 1e-5 * max(1.0, np.max(np.abs(f64)))
