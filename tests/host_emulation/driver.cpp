@@ -3,17 +3,18 @@
 // shared-memory sizes of the library's launchers and in the order the C ABI
 // issues them (test infrastructure).
 //
-//   driver rhs  nx ny nz prec gamma in.bin out.bin
+//   driver rhs  nx ny nz prec gamma in.bin out.bin [flux]
 //       R(y): face kernel, then the volume kernel in MODE_RHS (no driving)
-//   driver step nx ny nz prec gamma in.bin out.bin dt n_modes modes.bin c_iso rho0 lim_vol
+//   driver step nx ny nz prec gamma in.bin out.bin dt n_modes modes.bin c_iso rho0 lim_vol [flux]
 //       one dg_step (limiter of the input, three stages of face kernel,
 //       fused volume/stage kernel and queued limiter, with the driving field
 //       when n_modes > 0), then dg_energy_reset and the CFL reduction
 //
-//   driver hllc d gamma UL0..UL4 UR0..UR4
-//       the FP32 and FP64 HLLC fluxes of one face point
+//   driver hllc|exact d gamma UL0..UL4 UR0..UR4
+//       the FP32 and FP64 HLLC (or exact-Riemann) fluxes of one face point
 //
-// prec: 0 FP64, 1 mixed. States in the state layout [5][N][n_cells], FP64.
+// prec: 0 FP64, 1 mixed; flux: 0 HLLC (default), 1 exact Riemann solver.
+// States in the state layout [5][N][n_cells], FP64.
 // Prints "err=<device error word> dissipated=<...> smax=<...>".
 #include <type_traits>
 
@@ -66,14 +67,22 @@ static void make_setup(Setup& S, int nx, int ny, int nz, double gamma, int lim_v
   g.lim_vol = lim_vol;
 }
 
+// numerical flux: 0 HLLC, 1 exact Riemann solver (dg_set_flux)
+static int g_flux = 0;
+
 // face fluxes of the state ys (FP32 path: of its shadow yf)
-template <typename T>
-static void faces(Setup& S, const double* ys, float* yf, T* fh) {
+template <typename T, int FLUX>
+static void faces_f(Setup& S, const double* ys, float* yf, T* fh) {
   if constexpr (sizeof(T) == 4)
-    emu::launch(grid1(S.nc, 32), 96, 0, [&] { face_flux_f32_kernel<K, 0>(yf, fh, S.g, &S.ctrl); });
+    emu::launch(grid1(S.nc, 32), 96, 0, [&] { face_flux_f32_kernel<K, FLUX>(yf, fh, S.g, &S.ctrl); });
   else
     emu::launch(grid1(S.nc, 32), FaceSF64<K>::THREADS, FaceSF64<K>::smem(),
-                [&] { face_sf64_kernel<K, 0>(ys, fh, S.g, &S.ctrl); });
+                [&] { face_sf64_kernel<K, FLUX>(ys, fh, S.g, &S.ctrl); });
+}
+template <typename T>
+static void faces(Setup& S, const double* ys, float* yf, T* fh) {
+  if (g_flux) faces_f<T, 1>(S, ys, yf, fh);
+  else faces_f<T, 0>(S, ys, yf, fh);
 }
 
 // the volume kernel the launchers pick for (T, K) in MODE
@@ -188,8 +197,10 @@ static bool read_file(const char* path, double* p, size_t n) {
 }
 
 // driver hllc d gamma UL0..UL4 UR0..UR4: the FP32 and FP64 HLLC fluxes
+// (driver exact ...: the exact-Riemann-solver fluxes)
 static int run_hllc(int argc, char** argv) {
   if (argc != 14) return 2;
+  const bool exact = std::strcmp(argv[1], "exact") == 0;
   const int d = std::atoi(argv[2]);
   const double gamma = std::atof(argv[3]);
   float UL[5], UR[5], F[5];
@@ -200,18 +211,28 @@ static int run_hllc(int argc, char** argv) {
     UL[i] = (float)ULd[i];
     UR[i] = (float)URd[i];
   }
-  hllc_flux<float>(d, UL, UR, (float)gamma, F);
-  hllc_flux<double>(d, ULd, URd, gamma, Fd);
-  std::printf("f32=%.9g,%.9g,%.9g,%.9g,%.9g f64=%.17g,%.17g,%.17g,%.17g,%.17g\n", F[0], F[1], F[2], F[3], F[4],
-              Fd[0], Fd[1], Fd[2], Fd[3], Fd[4]);
+  unsigned e32 = 0, e64 = 0;
+  if (exact) {
+    e32 = riemann_flux<1, float>(d, UL, UR, (float)gamma, F);
+    e64 = riemann_flux<1, double>(d, ULd, URd, gamma, Fd);
+  } else {
+    hllc_flux<float>(d, UL, UR, (float)gamma, F);
+    hllc_flux<double>(d, ULd, URd, gamma, Fd);
+  }
+  std::printf("f32=%.9g,%.9g,%.9g,%.9g,%.9g f64=%.17g,%.17g,%.17g,%.17g,%.17g e32=%u e64=%u\n", F[0], F[1], F[2],
+              F[3], F[4], Fd[0], Fd[1], Fd[2], Fd[3], Fd[4], e32, e64);
   return 0;
 }
 
 int main(int argc, char** argv) {
-  if (argc >= 2 && std::strcmp(argv[1], "hllc") == 0) return run_hllc(argc, argv);
+  if (argc >= 2 && (std::strcmp(argv[1], "hllc") == 0 || std::strcmp(argv[1], "exact") == 0))
+    return run_hllc(argc, argv);
   if (argc < 9) return 2;
   const bool step = std::strcmp(argv[1], "step") == 0;
-  if (step ? argc != 15 : argc != 9) return 2;
+  // an optional last argument selects the numerical flux
+  const int nargs = step ? 15 : 9;
+  if (argc == nargs + 1) g_flux = std::atoi(argv[nargs]);
+  else if (argc != nargs) return 2;
   const int nx = std::atoi(argv[2]), ny = std::atoi(argv[3]), nz = std::atoi(argv[4]), prec = std::atoi(argv[5]);
   const double gamma = std::atof(argv[6]);
   Setup S;

@@ -193,3 +193,42 @@ def test_fp32_hllc_receding_vacuum_states(drivers):
         UR = _cons(rng.uniform(0.5, 2), rng.uniform(-1, 1, 3), rng.uniform(0.2, 2), g)
         f32, f64 = _hllc(exes[2], dirn, g, UL, UR, d)
         assert np.max(np.abs(f32 - f64)) <= 1e-5 * max(1.0, np.max(np.abs(f64)))
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_exact_flux_rhs_clean(drivers, k, prec):
+    """The exact-Riemann-solver face kernels (dg_set_flux) on strong jumps
+    between neighbouring cell means (limited first, as a step would)."""
+    d, exes = drivers
+    g = syn.GAMMA
+    w = syn.random_state(N_MESH, oracle.nmodes(k), g, seed=80 + k, high=0.1, rho_mean=(0.2, 2.0),
+                         v_mean=(-2.0, 2.0), p_mean=(0.1, 2.0))
+    o = oracle.Oracle(N_MESH, k, g, flux=oracle.FLUX_EXACT)
+    st, w, _, _ = o.limit(w)
+    assert st == 0
+    fin, fout = os.path.join(d, f"e{k}{prec}.in"), os.path.join(d, f"e{k}{prec}.out")
+    _layout(w).tofile(fin)
+    info = _run(exes[k], ["rhs", *N_MESH, prec, repr(g), fin, fout, 1], d)
+    assert info["err"] == "0"
+    R = _canonical(np.fromfile(fout), w.shape)
+    assert normwise(R, o.rhs(w)) <= (1e-12 if prec == 0 else 2e-5)
+
+
+@pytest.mark.parametrize("mode", ["hllc", "exact"])
+def test_fp32_fluxes_finite_near_vacuum(drivers, mode):
+    """Near-vacuum face states (pressures at, near or rounded below zero;
+    receding, approaching and resting flows; every direction): the FP32
+    fluxes are finite and the exact solver's Newton iteration converges."""
+    d, exes = drivers
+    g = syn.GAMMA
+    for pl, pr in ((-1e-4, -3e-4), (-2e-9, -6e-9), (1e-9, -6e-9), (0.0, 0.0), (1e-12, 1e-12), (1e-30, 1e-20)):
+        for ul, ur in ((-0.24, 0.12), (0.3, -0.2), (-2.0, 2.0), (0.0, 0.0)):
+            for dirn in range(3):
+                vL, vR = [0.0] * 3, [0.0] * 3
+                vL[dirn], vR[dirn] = ul, ur
+                vL[(dirn + 1) % 3] = 0.07
+                info = _run(exes[2], [mode, dirn, repr(g), *(repr(float(x)) for x in _cons(0.9989, vL, pl, g)),
+                                      *(repr(float(x)) for x in _cons(0.9451, vR, pr, g))], d)
+                f32 = np.array([float(x) for x in info["f32"].split(",")])
+                assert np.all(np.isfinite(f32)) and info["e32"] == "0", (mode, pl, pr, ul, ur, dirn, f32)
