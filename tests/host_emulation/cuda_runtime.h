@@ -5,3 +5,6 @@
 typedef int cudaError_t;
 typedef void* cudaStream_t;
 #define cudaSuccess 0
+struct double2 {
+  double x, y;
+};

@@ -10,6 +10,8 @@
 //       fused volume/stage kernel and queued limiter, with the driving field
 //       when n_modes > 0), then dg_energy_reset and the CFL reduction
 //
+//   driver analysis n gamma in.bin out.bin sub lo hi nb n_modes modes.bin spec.bin
+//       diagnostics, spectrum sampling and shell sums, density histogram
 //   driver hllc|exact d gamma UL0..UL4 UR0..UR4
 //       the FP32 and FP64 HLLC (or exact-Riemann) fluxes of one face point
 //
@@ -21,6 +23,11 @@
 #include "dg_kernels.cuh"
 using namespace dg;
 #include "tables.inc"
+namespace dg {
+namespace spec {
+#include "spectrum_kernels.inc"
+}  // namespace spec
+}  // namespace dg
 
 constexpr int K = DG_K;
 using TB = Tab<K>;
@@ -188,6 +195,30 @@ static void run_step(Setup& S, std::vector<double>& y, double dt, const std::vec
   std::printf("err=%u dissipated=%.17g smax=%.17g\n", S.ctrl.err, diss, smax);
 }
 
+// diagnostics partial sums (dg_diagnostics): out3 as the C ABI returns it
+template <typename T>
+static void run_diag(Setup& S, const std::vector<double>& y, const std::vector<double>& modes, int nm, double* out3) {
+  const long long nc = S.nc;
+  std::vector<T> field(nm > 0 ? (size_t)3 * TB::Q3 * nc : 1, T(0));
+  if (nm > 0)
+    emu::launch2(grid1(nc, kThreads), TB::Q3, kThreads, 0, [&] {
+      forcing_field_kernel<K, T>(field.data(), modes.data(), nm, S.t64.data(), S.g, 1.0, 1.0, 1.0);
+    });
+  const long long nb = (nc + 255) / 256;
+  const int G = (int)(nb < 1024 ? nb : 1024);
+  std::vector<double> part((size_t)3 * G, std::nan(""));
+  emu::launch(G, 256, 0, [&] {
+    diag_partial_kernel<K, T>(y.data(), field.data(), S.t64.data(), S.g, nm > 0 ? 1 : 0, part.data());
+  });
+  const double vol = S.g.dx[0] * S.g.dx[1] * S.g.dx[2];
+  double h[3] = {0, 0, 0};
+  for (int j = 0; j < 3; ++j)
+    for (int b = 0; b < G; ++b) h[j] += part[(size_t)j * G + b];
+  out3[0] = std::sqrt(h[0] * vol);
+  out3[1] = h[1] * vol;
+  out3[2] = h[2] * vol;
+}
+
 static bool read_file(const char* path, double* p, size_t n) {
   FILE* f = std::fopen(path, "rb");
   if (!f) return false;
@@ -224,9 +255,63 @@ static int run_hllc(int argc, char** argv) {
   return 0;
 }
 
+// driver analysis n gamma in.bin out.bin sub lo hi nb n_modes modes.bin spec.bin
+//   cubic mesh n^3: diagnostics (FP64 and FP32 field), the velocity samples
+//   of the three components, the ln(rho) histogram, and the shell sums of
+//   the three half spectra in spec.bin ([3][M][M][M/2+1] complex). out.bin:
+//   3 + 3 + 3 M^3 + (nb + 2) + n_bins(M) doubles.
+// the spectrum and PDF kernels are grid-stride loops (the library launches
+// 2048 / 1024 blocks); a grid of a few blocks runs the same per-thread index
+// arithmetic with more iterations per thread at a fraction of the emulation
+// cost
+constexpr unsigned kStrideGrid = 16;
+
+static int run_analysis(int argc, char** argv) {
+  if (argc != 13) return 2;
+  const int n = std::atoi(argv[2]), sub = std::atoi(argv[6]), nbins = std::atoi(argv[9]), nm = std::atoi(argv[10]);
+  const double gamma = std::atof(argv[3]), lo = std::atof(argv[7]), hi = std::atof(argv[8]);
+  Setup S;
+  make_setup(S, n, n, n, gamma, 0);
+  std::vector<double> y((size_t)5 * TB::N * S.nc), modes((size_t)9 * nm + 1);
+  if (!read_file(argv[4], y.data(), y.size())) return 3;
+  if (nm > 0 && !read_file(argv[11], modes.data(), (size_t)9 * nm)) return 3;
+  const int M = n * sub, H = M / 2 + 1;
+  const long long M3 = (long long)M * M * M;
+  const int nsh = (int)std::floor(std::sqrt(3.0) * M / 2.0) + 2;
+  std::vector<double> out;
+  double d3[3];
+  run_diag<double>(S, y, modes, nm, d3);
+  out.insert(out.end(), d3, d3 + 3);
+  run_diag<float>(S, y, modes, nm, d3);
+  out.insert(out.end(), d3, d3 + 3);
+  for (int comp = 0; comp < 3; ++comp) {
+    std::vector<double> v(M3, std::nan(""));
+    emu::launch(kStrideGrid, 256, 0, [&] { spec::sample_kernel(y.data(), K, n, sub, comp, v.data()); });
+    out.insert(out.end(), v.begin(), v.end());
+  }
+  std::vector<unsigned long long> counts(nbins + 2, 0);
+  emu::launch(kStrideGrid / 2, 256, sizeof(unsigned) * (nbins + 2),
+              [&] { spec::density_hist_kernel(y.data(), K, n, sub, lo, hi, nbins, counts.data()); });
+  for (auto c : counts) out.push_back((double)c);
+  std::vector<double2> sp((size_t)3 * M * M * H);
+  if (!read_file(argv[12], reinterpret_cast<double*>(sp.data()), sp.size() * 2)) return 3;
+  std::vector<double> bins(nsh, 0.0);
+  for (int comp = 0; comp < 3; ++comp)
+    emu::launch(kStrideGrid / 2, 256, sizeof(double) * nsh,
+                [&] { spec::bin_kernel(sp.data() + (size_t)comp * M * M * H, M, nsh, bins.data()); });
+  out.insert(out.end(), bins.begin(), bins.end());
+  FILE* f = std::fopen(argv[5], "wb");
+  if (!f) return 3;
+  std::fwrite(out.data(), 8, out.size(), f);
+  std::fclose(f);
+  std::printf("err=0 dissipated=0 smax=0\n");
+  return 0;
+}
+
 int main(int argc, char** argv) {
   if (argc >= 2 && (std::strcmp(argv[1], "hllc") == 0 || std::strcmp(argv[1], "exact") == 0))
     return run_hllc(argc, argv);
+  if (argc >= 2 && std::strcmp(argv[1], "analysis") == 0) return run_analysis(argc, argv);
   if (argc < 9) return 2;
   const bool step = std::strcmp(argv[1], "step") == 0;
   // an optional last argument selects the numerical flux

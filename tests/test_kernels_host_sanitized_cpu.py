@@ -4,7 +4,8 @@ under AddressSanitizer and UndefinedBehaviorSanitizer in a host emulation of
 the CUDA thread model (tests/host_emulation: one OS thread per CUDA thread,
 barriers for __syncthreads and warp shuffles, shared memory poisoned). Every
 global, shared and table access of the face, volume, stage, limiter, energy
-reset, forcing-field and CFL kernels is bounds-checked on meshes whose cell
+reset, forcing-field, CFL, diagnostics and spectrum/PDF kernels is
+bounds-checked on meshes whose cell
 count leaves ragged tiles, at every degree and in both precisions, with the
 launch sizes of the library's launchers and in the order the C ABI issues
 the kernels. The results are compared with the oracle only to confirm that
@@ -12,6 +13,7 @@ the emulation ran the kernels' arithmetic; parity of the GPU path itself is
 what the -m gpu tests check."""
 import concurrent.futures as cf
 import os
+import re
 import shutil
 import subprocess
 import tempfile
@@ -29,19 +31,35 @@ FLAGS = ["-std=c++20", "-O1", "-g", "-pthread", "-fsanitize=address,undefined", 
          "-fno-omit-frame-pointer"]
 
 
+_DYN_SMEM = re.compile(r"extern __shared__ (?:__align__\(\d+\) )?([A-Za-z_][\w ]*?) (\w+)\[\];")
+
+
+def _host_smem(src):
+    """Dynamic shared memory (extern __shared__ T name[];) taken from the
+    emulated block's buffer."""
+    s = _DYN_SMEM.sub(lambda m: f"{m.group(1)}* {m.group(2)} = reinterpret_cast<{m.group(1)}*>(emu::dyn_smem());",
+                      src)
+    assert "extern __shared__" not in s
+    return s
+
+
 def _generate(dst):
-    """The kernel headers with the dynamic shared memory taken from the
-    emulated block's buffer, and the table builder of dg_api.cu."""
+    """The kernel headers with host dynamic shared memory, the table builder
+    of dg_api.cu and the analysis kernels of dg_spectrum.cu."""
     for f in ("dg_common.cuh", "dg_kernels.cuh"):
-        s = open(os.path.join(CSRC, f)).read()
-        s = s.replace("extern __shared__ __align__(16) unsigned char smem_raw[];",
-                      "unsigned char* smem_raw = emu::dyn_smem();")
-        assert "extern __shared__" not in s, f
-        open(os.path.join(dst, f), "w").write(s)
+        open(os.path.join(dst, f), "w").write(_host_smem(open(os.path.join(CSRC, f)).read()))
     api = open(os.path.join(CSRC, "dg_api.cu")).read()
     a = api.index("// ----------------------------------------------------------------- tables")
     b = api.index("Launchers launchers_for(int k)")
     open(os.path.join(dst, "tables.inc"), "w").write(api[a:b] + "}  // namespace\n")
+    # the analysis kernels of dg_spectrum.cu (without the cuFFT plan helper)
+    sp = open(os.path.join(CSRC, "dg_spectrum.cu")).read()
+    a = sp.index("namespace {\n") + len("namespace {\n")
+    b = sp.index("}  // namespace\n", a)
+    body = sp[a:b]
+    p0 = body.index("// cuFFT plan of")
+    p1 = body.index("\n}\n", p0) + 3
+    open(os.path.join(dst, "spectrum_kernels.inc"), "w").write(_host_smem(body[:p0] + body[p1:]))
 
 
 @pytest.fixture(scope="module")
@@ -232,3 +250,40 @@ def test_fp32_fluxes_finite_near_vacuum(drivers, mode):
                                       *(repr(float(x)) for x in _cons(0.9451, vR, pr, g))], d)
                 f32 = np.array([float(x) for x in info["f32"].split(",")])
                 assert np.all(np.isfinite(f32)) and info["e32"] == "0", (mode, pl, pr, ul, ur, dirn, f32)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_analysis_kernels_clean(drivers, k):
+    """Diagnostics partial sums (FP64 and FP32 driving field), the velocity
+    sampling, ln(rho) histogram and shell-sum kernels of the spectrum and
+    PDF (the FFT between them taken by numpy), on a 3^3 mesh with 3^3
+    samples per cell."""
+    d, exes = drivers
+    g, n, sub, nb, lo, hi = syn.GAMMA, 3, 3, 24, -0.3, 0.3
+    N = oracle.nmodes(k)
+    w = syn.random_state((n, n, n), N, g, seed=90 + k, high=0.05)
+    nv = syn.driving_modes(1.0, 2.0)
+    ah = np.random.default_rng(91 + k).normal(size=(len(nv), 6)) * 0.5
+    o = oracle.Oracle((n, n, n), k, g)
+    o.set_forcing(nv, ah)
+    M = n * sub
+    vel = [o.sample_velocity(w, sub, c) for c in range(3)]
+    spec = np.stack([np.fft.rfftn(v) for v in vel])  # [3][M][M][M/2+1], layout [z][y][x]
+    fin, fout, fm, fs = (os.path.join(d, f"a{k}.{x}") for x in ("in", "out", "modes", "spec"))
+    _layout(w).tofile(fin)
+    np.ascontiguousarray(np.concatenate([nv.astype(np.float64), ah], axis=1)).tofile(fm)
+    np.ascontiguousarray(spec.astype(np.complex128)).view(np.float64).tofile(fs)
+    _run(exes[k], ["analysis", n, repr(g), fin, fout, sub, lo, hi, nb, len(nv), fm, fs], d)
+    out = np.fromfile(fout)
+    ref = o.diagnostics(w)
+    assert np.max(np.abs(out[0:3] - ref) / np.maximum(np.abs(ref), 1e-300)) <= 1e-12
+    assert np.max(np.abs(out[3:6] - ref) / np.maximum(np.abs(ref), 1e-300)) <= 1e-5
+    M3 = M ** 3
+    for c in range(3):
+        got = out[6 + c * M3: 6 + (c + 1) * M3]
+        assert np.max(np.abs(got - vel[c].ravel())) <= 1e-13 * np.max(np.abs(vel[c]))
+    cnt = out[6 + 3 * M3: 6 + 3 * M3 + nb + 2]
+    assert np.array_equal(cnt.astype(np.int64), o.density_pdf(w, sub, lo, hi, nb))
+    bins = out[6 + 3 * M3 + nb + 2:]
+    E = o.velocity_spectrum(w, sub)
+    assert len(bins) == len(E) and np.max(np.abs(bins - E)) <= 1e-12 * E.sum()
