@@ -287,3 +287,34 @@ def test_analysis_kernels_clean(drivers, k):
     bins = out[6 + 3 * M3 + nb + 2:]
     E = o.velocity_spectrum(w, sub)
     assert len(bins) == len(E) and np.max(np.abs(bins - E)) <= 1e-12 * E.sum()
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_kernels_race_free_under_tsan(k, tmp_path):
+    """The same kernels under ThreadSanitizer (shared-memory races between
+    the emulated CUDA threads of a block: a missing __syncthreads, a buffer
+    reused too early): R and a driven step with the limiter active, both
+    precisions."""
+    if shutil.which("g++") is None:
+        pytest.skip("g++ not available")
+    d = str(tmp_path)
+    _generate(d)
+    exe = os.path.join(d, "tsan")
+    flags = [f for f in FLAGS if not f.startswith("-fsanitize") and f != "-fno-sanitize-recover=undefined"]
+    r = subprocess.run(["g++", *flags, "-fsanitize=thread", "-I", EMU, "-I", d, "-include", os.path.join(EMU, "emu.h"),
+                        f"-DDG_K={k}", os.path.join(EMU, "driver.cpp"), "-o", exe], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-4000:]
+    g, n = syn.GAMMA, N_MESH
+    w = syn.random_state(n, oracle.nmodes(k), g, seed=100 + k, high=0.3)
+    fin, fout = os.path.join(d, "t.in"), os.path.join(d, "t.out")
+    _layout(w).tofile(fin)
+    st, dt = oracle.Oracle(n, k, g).cfl_dt(w, 0.3)
+    assert st == 0
+    for prec in (0, 1):
+        for args in (["rhs", *n, prec, repr(g), fin, fout],
+                     ["step", *n, prec, repr(g), fin, fout, repr(dt), 0, fin, 0.7, 1.0, 0]):
+            rr = subprocess.run([exe, *map(str, args)], capture_output=True, text=True, timeout=1800,
+                                env=dict(os.environ, TSAN_OPTIONS="halt_on_error=1"))
+            if "unexpected memory mapping" in rr.stderr:
+                pytest.skip("ThreadSanitizer cannot run on this host's memory layout")
+            assert rr.returncode == 0 and "WARNING: ThreadSanitizer" not in rr.stderr, rr.stderr[-4000:]
