@@ -262,7 +262,7 @@ void orc_hllc(int dir, double gamma, const double* UL, const double* UR, double*
     rho[s] = U[s][0];
     for (int a = 0; a < 3; ++a) vel[s][a] = U[s][1 + a] / rho[s];
     p[s] = pressure(gamma, U[s]);
-    c[s] = sqrt(gamma * p[s] / rho[s]);
+    c[s] = sqrt(fmax(gamma * p[s] / rho[s], 0.0)); /* 0 for a pressure rounded to <= 0 */
     H[s] = (U[s][4] + p[s]) / rho[s];
     un[s] = vel[s][dir];
   }
@@ -277,8 +277,10 @@ void orc_hllc(int dir, double gamma, const double* UL, const double* UR, double*
   double ct = c2t > 0.0 ? sqrt(c2t) : 0.0;
   double SL = fmin(un[0] - c[0], vt[dir] - ct);
   double SR = fmax(un[1] + c[1], vt[dir] + ct);
-  double Ss = (p[1] - p[0] + rho[0] * un[0] * (SL - un[0]) - rho[1] * un[1] * (SR - un[1])) /
-              (rho[0] * (SL - un[0]) - rho[1] * (SR - un[1]));
+  double den = rho[0] * (SL - un[0]) - rho[1] * (SR - un[1]);
+  /* den = 0 only when both sound speeds are 0 in a receding flow (S_L = u_L,
+   * S_R = u_R): no wave structure, S* = 0 */
+  double Ss = den != 0.0 ? (p[1] - p[0] + rho[0] * un[0] * (SL - un[0]) - rho[1] * un[1] * (SR - un[1])) / den : 0.0;
   if (SL >= 0.0) {
     orc_euler_flux(dir, gamma, UL, F);
     return;
@@ -295,7 +297,9 @@ void orc_hllc(int dir, double gamma, const double* UL, const double* UR, double*
   double Us[5];
   Us[0] = chi;
   for (int a = 0; a < 3; ++a) Us[1 + a] = chi * (a == dir ? Ss : vel[s][a]);
-  Us[4] = chi * (U[s][4] / rho[s] + (Ss - un[s]) * (Ss + p[s] / (rho[s] * (S - un[s]))));
+  /* E* = chi (E/rho + (S* - u)(S* + p / (rho (S - u)))), with
+   * chi / (rho (S - u)) = 1 / (S - S*) so that it stays defined for S = u */
+  Us[4] = chi * (U[s][4] / rho[s] + (Ss - un[s]) * Ss) + (Ss - un[s]) * p[s] / (S - Ss);
   for (int i = 0; i < 5; ++i) F[i] = Fs[i] + S * (Us[i] - U[s][i]);
 }
 

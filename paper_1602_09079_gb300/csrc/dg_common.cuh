@@ -192,16 +192,11 @@ __device__ __forceinline__ void hllc_flux(int d, const T* UL, const T* UR, T gam
   T vR[3] = {UR[1] * irR, UR[2] * irR, UR[3] * irR};
   T pL = gm1 * (UL[4] - T(0.5) * UL[0] * (vL[0] * vL[0] + vL[1] * vL[1] + vL[2] * vL[2]));
   T pR = gm1 * (UR[4] - T(0.5) * UR[0] * (vR[0] * vR[0] + vR[1] * vR[1] + vR[2] * vR[2]));
-  T cL, cR;
-  if constexpr (sizeof(T) == 4) {
-    // FP32 traces of a state limited in FP64 can round a pressure near the
-    // floor below zero: clamp the squared sound speeds
-    cL = sqrt(fmaxf(gamma * pL * irL, 0.f));
-    cR = sqrt(fmaxf(gamma * pR * irR, 0.f));
-  } else {
-    cL = sqrt(gamma * pL * irL);
-    cR = sqrt(gamma * pR * irR);
-  }
+  // a face pressure at the positivity floor can round to <= 0 (FP32 traces
+  // of an FP64-limited state; FP64 near vacuum when gamma - 1 is small): the
+  // sound speed is then 0, the limit p -> 0+
+  const T cL = sqrt(fmax(gamma * pL * irL, T(0)));
+  const T cR = sqrt(fmax(gamma * pR * irR, T(0)));
   const T sL = UL[0] * rL, sR = UR[0] * rR;
   T iss = T(1) / (sL + sR);
   T vt[3], v2 = T(0);
@@ -226,12 +221,10 @@ __device__ __forceinline__ void hllc_flux(int d, const T* UL, const T* UR, T gam
   }
   T aL = UL[0] * (SL - uL), aR = UR[0] * (SR - uR);
   T Ss = (pR - pL + uL * aL - uR * aR) / (aL - aR);
-  if constexpr (sizeof(T) == 4) {
-    // both FP32 pressures rounded to <= 0 (sound speeds clamped to zero) in
-    // a receding flow: S_L = u_L and S_R = u_R, so aL = aR = 0. Take S* = 0;
-    // the flux is then (0, p e_d, 0), the flux at a vacuum interface.
-    if (aL - aR == T(0)) Ss = T(0);
-  }
+  // both sound speeds 0 in a receding flow: S_L = u_L and S_R = u_R, so
+  // aL = aR = 0. Take S* = 0; the flux is then (0, p e_d, 0), the flux at a
+  // vacuum interface.
+  if (aL - aR == T(0)) Ss = T(0);
   const bool left = Ss >= T(0);
   const T* U = left ? UL : UR;
   const T* v = left ? vL : vR;
