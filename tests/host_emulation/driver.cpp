@@ -12,6 +12,10 @@
 //
 //   driver analysis n gamma in.bin out.bin sub lo hi nb n_modes modes.bin spec.bin
 //       diagnostics, spectrum sampling and shell sums, density histogram
+//   driver limit nx ny nz gamma eps lim_vol in.bin out.bin flags.bin
+//       dg_limit with per-cell flags
+//   driver project nx ny nz gamma first count f.bin out.bin
+//       dg_project_range
 //   driver hllc|exact d gamma UL0..UL4 UR0..UR4
 //       the FP32 and FP64 HLLC (or exact-Riemann) fluxes of one face point
 //
@@ -308,10 +312,54 @@ static int run_analysis(int argc, char** argv) {
   return 0;
 }
 
+// driver limit nx ny nz gamma eps lim_vol in.bin out.bin flags.bin
+//   the positivity limiter of dg_limit with per-cell flags (int8 file)
+// driver project nx ny nz gamma first count f.bin out.bin
+//   dg_project_range: f = [count][5][Q^3] point values of cells first..
+static int run_limit_project(int argc, char** argv) {
+  const bool lim = std::strcmp(argv[1], "limit") == 0;
+  if (argc != 11 && argc != 10) return 2;
+  const int nx = std::atoi(argv[2]), ny = std::atoi(argv[3]), nz = std::atoi(argv[4]);
+  const double gamma = std::atof(argv[5]);
+  Setup S;
+  make_setup(S, nx, ny, nz, gamma, lim ? std::atoi(argv[7]) : 0);
+  std::vector<double> y((size_t)5 * TB::N * S.nc, std::nan(""));
+  const char* out_path;
+  if (lim) {
+    if (argc != 11) return 2;
+    S.g.eps_rho = S.g.eps_p = std::atof(argv[6]);
+    if (!read_file(argv[8], y.data(), y.size())) return 3;
+    std::vector<int8_t> flags(S.nc, -1);
+    emu::launch(grid1(S.nc, kThreads), kThreads, 0,
+                [&] { limit_kernel<K>(y.data(), flags.data(), S.t64.data(), S.g, &S.ctrl); });
+    FILE* f = std::fopen(argv[10], "wb");
+    if (!f) return 3;
+    std::fwrite(flags.data(), 1, flags.size(), f);
+    std::fclose(f);
+    out_path = argv[9];
+  } else {
+    if (argc != 10) return 2;
+    const long long first = std::atoll(argv[6]), count = std::atoll(argv[7]);
+    std::vector<double> fv((size_t)count * 5 * TB::Q3);
+    if (!read_file(argv[8], fv.data(), fv.size())) return 3;
+    emu::launch(grid1(5 * count, kThreads), kThreads, 0,
+                [&] { project_kernel<K>(fv.data(), y.data(), S.t64.data(), S.g, first, count); });
+    out_path = argv[9];
+  }
+  FILE* f = std::fopen(out_path, "wb");
+  if (!f) return 3;
+  std::fwrite(y.data(), 8, y.size(), f);
+  std::fclose(f);
+  std::printf("err=%u n_limited=%llu\n", S.ctrl.err, (unsigned long long)S.ctrl.n_limited);
+  return 0;
+}
+
 int main(int argc, char** argv) {
   if (argc >= 2 && (std::strcmp(argv[1], "hllc") == 0 || std::strcmp(argv[1], "exact") == 0))
     return run_hllc(argc, argv);
   if (argc >= 2 && std::strcmp(argv[1], "analysis") == 0) return run_analysis(argc, argv);
+  if (argc >= 2 && (std::strcmp(argv[1], "limit") == 0 || std::strcmp(argv[1], "project") == 0))
+    return run_limit_project(argc, argv);
   if (argc < 9) return 2;
   const bool step = std::strcmp(argv[1], "step") == 0;
   // an optional last argument selects the numerical flux

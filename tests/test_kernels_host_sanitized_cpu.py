@@ -318,3 +318,44 @@ def test_kernels_race_free_under_tsan(k, tmp_path):
             if "unexpected memory mapping" in rr.stderr:
                 pytest.skip("ThreadSanitizer cannot run on this host's memory layout")
             assert rr.returncode == 0 and "WARNING: ThreadSanitizer" not in rr.stderr, rr.stderr[-4000:]
+
+
+@pytest.mark.parametrize("lim_vol", [0, 1])
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_limiter_with_flags_clean(drivers, k, lim_vol):
+    """dg_limit's kernel with per-cell flags on states whose polynomials
+    leave the positive set (floors 1e-2), both point sets: flags bit-exact
+    and the state within 1e-12 of the oracle's limiter."""
+    d, exes = drivers
+    g, n, eps = 1.4, N_MESH, 1e-2
+    w = syn.random_state(n, oracle.nmodes(k), g, seed=110 + k, high=0.5)
+    o = oracle.Oracle(n, k, g, eps_rho=eps, eps_p=eps, limiter_points=lim_vol)
+    st, ref, fref, nref = o.limit(w)
+    assert st == 0 and nref > 5
+    fin, fout, ffl = (os.path.join(d, f"l{k}{lim_vol}.{x}") for x in ("in", "out", "flags"))
+    _layout(w).tofile(fin)
+    info = _run(exes[k], ["limit", *n, repr(g), repr(eps), lim_vol, fin, fout, ffl], d)
+    assert info["err"] == "0" and int(info["n_limited"]) == nref
+    assert np.array_equal(np.fromfile(ffl, dtype=np.int8), np.asarray(fref, dtype=np.int8).ravel())
+    assert normwise(_canonical(np.fromfile(fout), w.shape), ref) <= 1e-12
+
+
+@pytest.mark.parametrize("k", [0, 1, 2, 3])
+def test_projection_range_clean(drivers, k):
+    """dg_project_range's kernel on a range of cells that ends in a ragged
+    block: the projected weights of those cells equal the oracle's
+    projection of the same point values."""
+    d, exes = drivers
+    g, n = syn.GAMMA, N_MESH
+    o = oracle.Oracle(n, k, g)
+    fn = syn.solenoidal_velocity(seed=5, mach=0.3)
+    xyz = o.volume_points()
+    vals = np.moveaxis(np.asarray(fn(xyz[..., 0], xyz[..., 1], xyz[..., 2])), 0, 1)  # [nc][5][Q^3]
+    ref = o.project(vals).reshape(o.ncells, 5, -1)
+    first, count = 17, 61
+    fin, fout = os.path.join(d, f"p{k}.in"), os.path.join(d, f"p{k}.out")
+    np.ascontiguousarray(vals[first:first + count]).tofile(fin)
+    _run(exes[k], ["project", *n, repr(g), first, count, fin, fout], d)
+    y = _canonical(np.fromfile(fout), (n[2], n[1], n[0], 5, oracle.nmodes(k))).reshape(o.ncells, 5, -1)
+    assert np.all(np.isnan(y[:first])) and np.all(np.isnan(y[first + count:]))  # other cells untouched
+    assert np.max(np.abs(y[first:first + count] - ref[first:first + count])) <= 1e-14 * np.max(np.abs(ref))
