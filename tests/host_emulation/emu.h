@@ -38,6 +38,7 @@ struct Block {
   std::vector<std::unique_ptr<std::barrier<>>> warp;
   std::vector<unsigned char> smem;
   std::vector<uint64_t> shfl;
+  std::vector<uint32_t> mma;  // per thread: 4 A and 2 B fragment registers
 };
 inline emu_uint3 g_blockIdx, g_blockDim, g_gridDim;
 inline thread_local emu_uint3 t_threadIdx;
@@ -63,6 +64,7 @@ void launch2(unsigned grid, unsigned gridy, unsigned block, size_t smem, F&& f) 
       B.warp.push_back(std::make_unique<std::barrier<>>(std::min(32u, block - 32 * w)));
     B.smem.assign(smem + 16, 0xCD);  // poison: reads before writes show up
     B.shfl.assign(block, 0);
+    B.mma.assign((size_t)6 * block, 0);
     g_block = &B;
   };
   std::vector<std::thread> th;
@@ -150,6 +152,98 @@ inline int __double2loint(double x) { return (int)(unsigned)((unsigned long long
 inline double __hiloint2double(int hi, int lo) {
   return __longlong_as_double((long long)(((unsigned long long)(unsigned)hi << 32) | (unsigned)lo));
 }
+inline float atomicAdd(float* p, float v) {
+  float old, nw;
+  unsigned ob, nb;
+  do {
+    std::memcpy(&ob, p, 4);
+    std::memcpy(&old, &ob, 4);
+    nw = old + v;
+    std::memcpy(&nb, &nw, 4);
+  } while (!__atomic_compare_exchange_n((unsigned*)p, &ob, nb, false, __ATOMIC_SEQ_CST, __ATOMIC_SEQ_CST));
+  return old;
+}
+
+// BF16 storage type and round-to-nearest-even conversions
+struct __nv_bfloat16 {
+  uint16_t x;
+};
+struct __nv_bfloat162 {
+  __nv_bfloat16 x, y;
+};
+inline __nv_bfloat16 __float2bfloat16(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  __nv_bfloat16 h;
+  if ((u & 0x7fffffffu) > 0x7f800000u) {
+    h.x = 0x7fc0;  // NaN
+    return h;
+  }
+  u += 0x7fffu + ((u >> 16) & 1u);
+  h.x = (uint16_t)(u >> 16);
+  return h;
+}
+inline __nv_bfloat16 __double2bfloat16(double d) {
+  // round the binary64 significand to 8 bits directly (no intermediate
+  // binary32 rounding); normal range of the test data only
+  uint64_t u;
+  std::memcpy(&u, &d, 8);
+  if (d != d) return __float2bfloat16(NAN);
+  if (d == 0.0) return __float2bfloat16(std::signbit(d) ? -0.f : 0.f);
+  int e;
+  const double m = std::frexp(std::fabs(d), &e);       // |d| = m 2^e, m in [0.5, 1)
+  const double q = std::nearbyint(std::ldexp(m, 8));    // 8 significant bits, ties to even
+  return __float2bfloat16((float)std::copysign(std::ldexp(q, e - 8), d));
+}
+inline float __bfloat162float(__nv_bfloat16 h) {
+  const uint32_t u = (uint32_t)h.x << 16;
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+inline __nv_bfloat162 __floats2bfloat162_rn(float lo, float hi) { return {__float2bfloat16(lo), __float2bfloat16(hi)}; }
+struct uint4 {
+  unsigned x, y, z, w;
+};
+inline uint4 make_uint4(unsigned x, unsigned y, unsigned z, unsigned w) { return {x, y, z, w}; }
+inline float __expf(float x) { return std::exp(x); }
+
+namespace emu {
+// mma.sync m16n8k16 row.col, BF16 inputs, FP32 accumulate, over the warp:
+// lane (g = lane / 4, t = lane % 4) holds A[g][2t..2t+1], A[g+8][2t..],
+// A[g][2t+8..], A[g+8][2t+8..] (a0..a3), B[2t..2t+1][g], B[2t+8..][g]
+// (b0, b1), and D[g][2t..2t+1], D[g+8][2t..2t+1] (d0..d3); the lower 16 bits
+// of a register hold the element with the even k
+inline float bf_lo(uint32_t v) { return __uint_as_float(v << 16); }
+inline float bf_hi(uint32_t v) { return __uint_as_float(v & 0xffff0000u); }
+inline void mma_bf16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  const unsigned tid = threadIdx.x, w = tid / 32, lane = tid % 32;
+  auto& B = *g_block;
+  uint32_t* mine = &B.mma[(size_t)6 * tid];
+  for (int i = 0; i < 4; ++i) mine[i] = a[i];
+  mine[4] = b[0];
+  mine[5] = b[1];
+  B.warp[w]->arrive_and_wait();
+  const uint32_t* base = &B.mma[(size_t)6 * (w * 32)];
+  auto A = [&](int r, int k) {
+    const uint32_t reg = base[6 * ((r % 8) * 4 + (k % 8) / 2) + (r >= 8 ? 1 : 0) + (k >= 8 ? 2 : 0)];
+    return (k % 2) ? bf_hi(reg) : bf_lo(reg);
+  };
+  auto Bm = [&](int k, int n) {
+    const uint32_t reg = base[6 * (n * 4 + (k % 8) / 2) + 4 + (k >= 8 ? 1 : 0)];
+    return (k % 2) ? bf_hi(reg) : bf_lo(reg);
+  };
+  const int g = lane / 4, t = lane % 4;
+  for (int i = 0; i < 4; ++i) {
+    const int r = g + (i >= 2 ? 8 : 0), n = 2 * t + (i % 2);
+    float acc = d[i];
+    for (int k = 0; k < 16; ++k) acc += A(r, k) * Bm(k, n);
+    d[i] = acc;
+  }
+  B.warp[w]->arrive_and_wait();
+}
+}  // namespace emu
+
 inline double rsqrt(double x) { return 1.0 / std::sqrt(x); }
 inline float rsqrtf(float x) { return 1.0f / std::sqrt(x); }
 using std::cbrt;

@@ -60,6 +60,18 @@ def _generate(dst):
     p0 = body.index("// cuFFT plan of")
     p1 = body.index("\n}\n", p0) + 3
     open(os.path.join(dst, "spectrum_kernels.inc"), "w").write(_host_smem(body[:p0] + body[p1:]))
+    # the indicator's kernels (dg_mlp.cu up to its host dispatch), with the
+    # inline-PTX mma.sync replaced by the emulation's warp-level product
+    ml = open(os.path.join(CSRC, "dg_mlp.cu")).read()
+    a = ml.index("namespace {\n") + len("namespace {\n")
+    b = ml.index("// ------------------------------------------------------------ dispatch")
+    body = ml[a:b]
+    m0 = body.index("__device__ __forceinline__ void mma(")
+    m1 = body.index("\n}\n", m0) + 3
+    body = body[:m0] + ("__device__ __forceinline__ void mma(float (&d)[4], const uint32_t (&a)[4], "
+                        "const uint32_t (&b)[2]) {\n  emu::mma_bf16(d, a, b);\n}\n") + body[m1:]
+    assert "asm" not in body
+    open(os.path.join(dst, "mlp_kernels.inc"), "w").write(_host_smem(body))
 
 
 @pytest.fixture(scope="module")
@@ -359,3 +371,85 @@ def test_projection_range_clean(drivers, k):
     y = _canonical(np.fromfile(fout), (n[2], n[1], n[0], 5, oracle.nmodes(k))).reshape(o.ncells, 5, -1)
     assert np.all(np.isnan(y[:first])) and np.all(np.isnan(y[first + count:]))  # other cells untouched
     assert np.max(np.abs(y[first:first + count] - ref[first:first + count])) <= 1e-14 * np.max(np.abs(ref))
+
+
+@pytest.fixture(scope="module")
+def mlp_drivers(drivers):
+    d, _ = drivers
+
+    def build(k):
+        exe = os.path.join(d, f"mlp_k{k}")
+        cmd = ["g++", *FLAGS, "-I", EMU, "-I", d, "-include", os.path.join(EMU, "emu.h"), f"-DDG_K={k}",
+               os.path.join(EMU, "mlp_driver.cpp"), "-o", exe]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr[-4000:]
+        return exe
+
+    with cf.ThreadPoolExecutor(3) as ex:
+        exes = dict(zip((1, 2, 3), ex.map(build, (1, 2, 3))))
+    return d, exes
+
+
+@pytest.mark.parametrize("order", [2, 3, 4])
+def test_indicator_kernels_clean(mlp_drivers, order):
+    """The learned indicator's features, BF16 forward and backward kernels
+    (mma.sync m16n8k16 emulated at the warp from its documented fragment
+    layout): bounds-checked, and within the GPU tests' criteria of the
+    oracle (features within one BF16 ulp, logits within 5e-3 of their scale,
+    gradients within 2e-2 relative L2 and 0.999 cosine)."""
+    torch = pytest.importorskip("torch")
+    import test_gpu_indicator as T  # the mirrored-oracle helpers (numpy / torch on the CPU)
+    from oracle import mlp
+    d, exes = mlp_drivers
+    k, g = order - 1, syn.GAMMA
+    F = mlp.n_features_padded(k)
+    exe = exes[k]
+
+    def bits(a):
+        return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(torch.bfloat16).view(torch.int16).numpy()
+
+    def unbits(b):
+        return torch.from_numpy(b).view(torch.bfloat16).to(torch.float64).numpy()
+
+    n = (7, 6, 5)
+    nc = n[0] * n[1] * n[2]
+    w = syn.random_state(n, oracle.nmodes(k), g, seed=120 + order, high=0.05)
+    f = lambda x: os.path.join(d, f"i{order}.{x}")  # noqa: E731
+    _layout(w).tofile(f("in"))
+    _run_plain(exe, ["features", *n, repr(g), f("in"), f("X")], d)
+    got = unbits(np.fromfile(f("X"), dtype=np.int16).reshape(nc, F))
+    ref = T.bf16(mlp.features(w, k, g))
+    assert np.all(np.abs(got - ref) <= np.abs(ref) * 2.0 ** -7 + 1e-30)
+
+    rng = np.random.default_rng(130 + order)
+    N = 300  # three 128-row tiles, the last ragged
+    X = T.bf16(rng.normal(size=(N, F)))
+    P = T.rand_params(F, 131 + order)
+    bits(X).tofile(f("fx"))
+    T.flat(P).tofile(f("P"))
+    _run_plain(exe, ["forward", N, f("fx"), f("P"), f("lg")], d)
+    lg = np.fromfile(f("lg"), dtype=np.float32).astype(np.float64)
+    Q = T.mirrored(P)
+    cache = T.forward_mirrored(Q, X)
+    assert np.all(np.isfinite(lg))
+    assert np.max(np.abs(lg - cache["logit"])) <= 5e-3 * np.max(np.abs(cache["logit"])) + 1e-4
+
+    y = (rng.uniform(size=N) < 0.3).astype(np.float64)
+    a = 3.0
+    y.astype(np.float32).tofile(f("y"))
+    _run_plain(exe, ["backward", N, repr(a), f("fx"), f("y"), f("P"), f("G")], d)
+    gv = np.fromfile(f("G"), dtype=np.float32).astype(np.float64)
+    npar = len(T.flat(P))
+    assert abs(gv[npar] - mlp.loss(cache["logit"], y, a)) <= 1e-3 * abs(mlp.loss(cache["logit"], y, a))
+    got = T.unflat(gv[:npar], F)
+    gref = mlp.backward(Q, X, cache, y, a)
+    for key in gref:
+        r, q = gref[key].ravel(), got[key].ravel()
+        rel = np.linalg.norm(q - r) / max(np.linalg.norm(r), 1e-30)
+        cos = q @ r / max(np.linalg.norm(q) * np.linalg.norm(r), 1e-30)
+        assert rel <= 2e-2 and cos >= 0.999, (key, rel, cos)
+
+
+def _run_plain(exe, args, d):
+    r = subprocess.run([exe, *map(str, args)], capture_output=True, text=True, timeout=900, cwd=d)
+    assert r.returncode == 0, (r.returncode, r.stderr[-4000:])
