@@ -453,3 +453,48 @@ def test_indicator_kernels_clean(mlp_drivers, order):
 def _run_plain(exe, args, d):
     r = subprocess.run([exe, *map(str, args)], capture_output=True, text=True, timeout=900, cwd=d)
     assert r.returncode == 0, (r.returncode, r.stderr[-4000:])
+
+
+def test_indicator_gate_and_adam_clean(mlp_drivers):
+    """The gate kernel (features and forward of the limiter queue, cells
+    whose logit reaches the threshold appended with atomics) and the Adam
+    kernel, order 3: the gated set equals the oracle's away from the
+    threshold; Adam equals the update written out in numpy."""
+    pytest.importorskip("torch")
+    import test_gpu_indicator as T
+    from oracle import mlp
+    d, exes = mlp_drivers
+    k, g, n = 2, syn.GAMMA, (7, 6, 5)
+    nc = n[0] * n[1] * n[2]
+    F = mlp.n_features_padded(k)
+    w = syn.random_state(n, oracle.nmodes(k), g, seed=140, high=0.05)
+    P = T.rand_params(F, 141)
+    queue = np.sort(np.random.default_rng(142).choice(nc, size=150, replace=False)).astype(np.int32)
+    logit = T.forward_mirrored(T.mirrored(P), T.bf16(mlp.features(w, k, g)[queue]))["logit"]
+    thr = float(np.median(logit))
+    f = lambda x: os.path.join(d, f"gate.{x}")  # noqa: E731
+    _layout(w).tofile(f("in"))
+    queue.tofile(f("list"))
+    T.flat(P).tofile(f("P"))
+    _run_plain(exes[k], ["gate", *n, repr(g), f("in"), f("list"), len(queue), f("P"), repr(thr), f("out")], d)
+    got = set(np.fromfile(f("out"), dtype=np.int32).tolist())
+    margin = 5e-3 * np.max(np.abs(logit)) + 1e-4
+    assert set(queue[logit >= thr + margin].tolist()) <= got
+    assert not (got & set(queue[logit < thr - margin].tolist()))
+    assert got <= set(queue.tolist())
+
+    rng = np.random.default_rng(143)
+    m_ = 1000
+    p, m, v, gr = (rng.normal(size=m_).astype(np.float32) for _ in range(4))
+    v = np.abs(v)
+    for arr, x in ((p, "p"), (m, "m"), (v, "v"), (gr, "g")):
+        arr.tofile(f(x))
+    step, lr = 3, 1e-3
+    _run_plain(exes[k], ["adam", m_, step, repr(lr), f("p"), f("m"), f("v"), f("g")], d)
+    out = np.fromfile(f("g"), dtype=np.float32).reshape(3, m_).astype(np.float64)
+    b1, b2, eps = 0.9, 0.999, 1e-8
+    m1 = b1 * m + (1 - b1) * gr
+    v1 = b2 * v + (1 - b2) * gr.astype(np.float64) ** 2
+    p1 = p - lr * (m1 / (1 - b1 ** step)) / (np.sqrt(v1 / (1 - b2 ** step)) + eps)
+    for got_, ref in zip(out, (p1, m1, v1)):
+        assert np.max(np.abs(got_ - ref)) <= 1e-5 * max(1.0, np.max(np.abs(ref)))
