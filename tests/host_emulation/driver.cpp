@@ -16,6 +16,8 @@
 //       dg_limit with per-cell flags
 //   driver project nx ny nz gamma first count f.bin out.bin
 //       dg_project_range
+//   driver layout nx ny nz in.bin out.bin
+//       canonical <-> state transposes and the conserved totals
 //   driver hllc|exact d gamma UL0..UL4 UR0..UR4
 //       the FP32 and FP64 HLLC (or exact-Riemann) fluxes of one face point
 //
@@ -32,6 +34,9 @@ namespace spec {
 #include "spectrum_kernels.inc"
 }  // namespace spec
 }  // namespace dg
+namespace api {
+#include "api_kernels.inc"
+}  // namespace api
 
 constexpr int K = DG_K;
 using TB = Tab<K>;
@@ -354,10 +359,43 @@ static int run_limit_project(int argc, char** argv) {
   return 0;
 }
 
+// driver layout nx ny nz in.bin out.bin
+//   canonical -> state -> canonical through the C ABI's transpose kernels,
+//   then the five conserved totals (means_partial + sum_rows); out.bin: the
+//   state layout, the round trip and the totals
+static int run_layout(int argc, char** argv) {
+  if (argc != 7) return 2;
+  const int nx = std::atoi(argv[2]), ny = std::atoi(argv[3]), nz = std::atoi(argv[4]);
+  const long long nc = (long long)nx * ny * nz;
+  const int N = TB::N, R = 5 * N;
+  std::vector<double> canon((size_t)nc * R), st((size_t)nc * R, std::nan("")), back((size_t)nc * R, std::nan(""));
+  if (!read_file(argv[5], canon.data(), canon.size())) return 3;
+  const unsigned gx = (unsigned)((nc + 31) / 32), gy = (unsigned)((R + 31) / 32);
+  emu::launch2(gx, gy, 256, 0, [&] { api::canon_to_state_kernel(canon.data(), st.data(), nc, R); }, 8);
+  emu::launch2(gx, gy, 256, 0, [&] { api::state_to_canon_kernel(st.data(), back.data(), nc, R); }, 8);
+  const long long nb = (nc + 255) / 256;
+  const int G = (int)(nb < api::kRedBlocks ? nb : api::kRedBlocks);
+  std::vector<double> part((size_t)5 * G, std::nan("")), sums(5, std::nan(""));
+  emu::launch(G, 256, 0, [&] { api::means_partial_kernel(st.data(), nc, N, part.data()); });
+  const double vol = 1.0 / (double)nc;
+  emu::launch(5, 256, 0, [&] { api::sum_rows_kernel(part.data(), G, vol, sums.data()); });
+  std::vector<double> out;
+  out.insert(out.end(), st.begin(), st.end());
+  out.insert(out.end(), back.begin(), back.end());
+  out.insert(out.end(), sums.begin(), sums.end());
+  FILE* f = std::fopen(argv[6], "wb");
+  if (!f) return 3;
+  std::fwrite(out.data(), 8, out.size(), f);
+  std::fclose(f);
+  std::printf("err=0\n");
+  return 0;
+}
+
 int main(int argc, char** argv) {
   if (argc >= 2 && (std::strcmp(argv[1], "hllc") == 0 || std::strcmp(argv[1], "exact") == 0))
     return run_hllc(argc, argv);
   if (argc >= 2 && std::strcmp(argv[1], "analysis") == 0) return run_analysis(argc, argv);
+  if (argc >= 2 && std::strcmp(argv[1], "layout") == 0) return run_layout(argc, argv);
   if (argc >= 2 && (std::strcmp(argv[1], "limit") == 0 || std::strcmp(argv[1], "project") == 0))
     return run_limit_project(argc, argv);
   if (argc < 9) return 2;

@@ -47,9 +47,10 @@ inline unsigned char* dyn_smem() { return g_block->smem.data(); }
 
 // run f() as grid x block threads (1D), dynamic shared memory of smem bytes
 template <class F>
-void launch2(unsigned grid, unsigned gridy, unsigned block, size_t smem, F&& f) {
+void launch2(unsigned grid, unsigned gridy, unsigned block, size_t smem, F&& f, unsigned blocky = 1) {
+  // block = threads per block; with blocky > 1 the block is (block / blocky) x blocky
   g_gridDim = {grid, gridy, 1};
-  g_blockDim = {block, 1, 1};
+  g_blockDim = {block / blocky, blocky, 1};
   const unsigned nblocks = grid * gridy, nw = (block + 31) / 32;
   // one pool of `block` threads walks the blocks; the main thread sets each
   // block up (fresh barriers, poisoned shared memory) between two pool-wide
@@ -71,7 +72,7 @@ void launch2(unsigned grid, unsigned gridy, unsigned block, size_t smem, F&& f) 
   th.reserve(block);
   for (unsigned t = 0; t < block; ++t)
     th.emplace_back([&, t] {
-      t_threadIdx = {t, 0, 0};
+      t_threadIdx = {t % (block / blocky), t / (block / blocky), 0};
       for (unsigned bb = 0; bb < nblocks; ++bb) {
         start.arrive_and_wait();
         f();
@@ -100,10 +101,12 @@ void launch(unsigned grid, unsigned block, size_t smem, F&& f) {
 #define gridDim (emu::g_gridDim)
 
 inline void __syncthreads() { emu::g_block->bar->arrive_and_wait(); }
+// linear thread index within the block (warps are formed from it)
+inline unsigned emu_linear_tid() { return threadIdx.x + threadIdx.y * blockDim.x; }
 
 template <class T>
 inline T __shfl_xor_sync(unsigned, T v, int m) {
-  const unsigned t = threadIdx.x, w = t / 32, lane = t % 32;
+  const unsigned t = emu_linear_tid(), w = t / 32, lane = t % 32;
   auto& B = *emu::g_block;
   uint64_t bits = 0;
   std::memcpy(&bits, &v, sizeof(T));
@@ -217,7 +220,7 @@ namespace emu {
 inline float bf_lo(uint32_t v) { return __uint_as_float(v << 16); }
 inline float bf_hi(uint32_t v) { return __uint_as_float(v & 0xffff0000u); }
 inline void mma_bf16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-  const unsigned tid = threadIdx.x, w = tid / 32, lane = tid % 32;
+  const unsigned tid = emu_linear_tid(), w = tid / 32, lane = tid % 32;
   auto& B = *g_block;
   uint32_t* mine = &B.mma[(size_t)6 * tid];
   for (int i = 0; i < 4; ++i) mine[i] = a[i];

@@ -60,6 +60,10 @@ def _generate(dst):
     p0 = body.index("// cuFFT plan of")
     p1 = body.index("\n}\n", p0) + 3
     open(os.path.join(dst, "spectrum_kernels.inc"), "w").write(_host_smem(body[:p0] + body[p1:]))
+    # the C ABI's own helper kernels (layout transposes, reductions)
+    a = api.index("// ------------------------------------------------------ helper kernels")
+    b = api.index("size_t align256(size_t b)")
+    open(os.path.join(dst, "api_kernels.inc"), "w").write(_host_smem(api[a:b]))
     # the indicator's kernels (dg_mlp.cu up to its host dispatch), with the
     # inline-PTX mma.sync replaced by the emulation's warp-level product
     ml = open(os.path.join(CSRC, "dg_mlp.cu")).read()
@@ -498,3 +502,24 @@ def test_indicator_gate_and_adam_clean(mlp_drivers):
     p1 = p - lr * (m1 / (1 - b1 ** step)) / (np.sqrt(v1 / (1 - b2 ** step)) + eps)
     for got_, ref in zip(out, (p1, m1, v1)):
         assert np.max(np.abs(got_ - ref)) <= 1e-5 * max(1.0, np.max(np.abs(ref)))
+
+
+@pytest.mark.parametrize("k", [1, 3])
+def test_layout_and_totals_kernels_clean(drivers, k):
+    """The C ABI's canonical <-> state transposes (32 x 8 thread blocks,
+    32 x 33 shared tiles; ragged in cells and in rows 5 N) round-trip a
+    state exactly, and the totals reduction matches the cell-mean sums."""
+    d, exes = drivers
+    n = (5, 3, 7)
+    nc = n[0] * n[1] * n[2]
+    w = syn.random_state(n, oracle.nmodes(k), syn.GAMMA, seed=150 + k, high=0.1)
+    fin, fout = os.path.join(d, f"y{k}.in"), os.path.join(d, f"y{k}.out")
+    np.ascontiguousarray(w).tofile(fin)
+    _run_plain(exes[k], ["layout", *n, fin, fout], d)
+    out = np.fromfile(fout)
+    R = 5 * oracle.nmodes(k)
+    st, back, sums = out[:nc * R], out[nc * R:2 * nc * R], out[2 * nc * R:]
+    assert np.array_equal(st, _layout(w).ravel())
+    assert np.array_equal(back, w.ravel())
+    ref = w.reshape(nc, 5, -1)[:, :, 0].sum(axis=0) / nc
+    assert np.max(np.abs(sums - ref)) <= 1e-14 * np.max(np.abs(ref))
