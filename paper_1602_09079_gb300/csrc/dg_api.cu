@@ -198,6 +198,14 @@ Launchers launchers_for(int k) {
   }
 }
 
+// fused FP32-mixed stage kernels exist for degree 2
+FusedLaunchers fused_for(int k) {
+  if (k == 2) return fused_launchers_k2();
+  FusedLaunchers L{};
+  L.k = k;
+  return L;
+}
+
 std::mutex g_upload_mu;
 unsigned long long g_uploaded[4] = {0, 0, 0, 0};  // bit per device
 
@@ -215,6 +223,8 @@ int upload_tables(int k, int dev) {
   for (int i = 0; i < TAB_STRIDE; ++i) t32[i] = (float)t64[i];
   Launchers L = launchers_for(k);
   if (L.upload(t64.data(), t32.data()) != cudaSuccess) return DG_ERR_CUDA;
+  FusedLaunchers F = fused_for(k);
+  if (F.upload && F.upload(t64.data()) != cudaSuccess) return DG_ERR_CUDA;
   if (dev >= 0 && dev < 64) g_uploaded[k] |= 1ull << dev;
   return DG_OK;
 }
@@ -319,6 +329,7 @@ struct dg_ctx {
   Geo geo{};
   double L[3] = {1, 1, 1};
   Launchers fn{};
+  FusedLaunchers fz{};  // fused FP32-mixed stage kernels (fz.run null: none for this degree)
   // binding
   bool bound = false;
   double* y = nullptr;
@@ -334,7 +345,11 @@ struct dg_ctx {
   double* ybuf = nullptr;
   int* list = nullptr;
   int* list2 = nullptr;
-  float* yf = nullptr;        // FP32 shadow of the state (FP32 path, degrees <= 2)
+  float* yf = nullptr;        // FP32 shadow of the state (FP32 path)
+  // fused mixed path: second stage buffer and the FP32 increment y_s - y_0
+  // of the step (both carved from the face-flux area, which it does not use)
+  double* ybuf2 = nullptr;
+  float* dinc = nullptr;
   bool shadow_valid = false;  // yf == float(y)
   // learned indicator gate (caller-owned FP32 parameters)
   const float* ind_params = nullptr;
@@ -466,6 +481,10 @@ enum { KC_LIMIT = 0, KC_FACE = 1, KC_VOLUME = 2, KC_CFL = 3, KC_RESET = 4, KC_OT
 // true when the current precision's kernels read the FP32 shadow
 bool uses_shadow(const dg_ctx* c) { return c->prec == DG_PREC_MIXED && c->fn.f32_shadow; }
 
+// true when the mixed path runs the fused stage kernels (they read the FP64
+// state; the FP32 shadow is written by the last stage only)
+bool uses_fused(const dg_ctx* c) { return c->prec == DG_PREC_MIXED && c->fz.run && c->ybuf2 && c->dinc; }
+
 // yf = float(y) (y: the bound state or any state-layout buffer)
 int convert_shadow(dg_ctx* c, const double* y) {
   const long long n = (long long)5 * c->N * c->geo.nc;
@@ -499,6 +518,55 @@ __global__ void __launch_bounds__(256) fma_probe_kernel(int iters, T a, T b, int
     if (sizeof(T) == 8) g_probe_sink64 = (double)s;
     else g_probe_sink32 = (float)s;
   }
+}
+
+// One SSP-RK3 step on the fused mixed path: three stage launches
+// y -> ybuf -> ybuf2 -> y (a stage never writes the buffer it reads, whose
+// neighbours other tiles read), each followed by the full limiter on the
+// cells that failed the stage's screen. Stages 1-2 keep the FP32 increment
+// d = y_s - y_0 for the next stage's combination; the limiter recomputes it
+// for the cells it changes. The last stage writes the FP32 shadow.
+int fused_step(dg_ctx* c, double dt, bool force) {
+  const double a0[3] = {0.0, 0.75, 1.0 / 3.0};
+  const double b0[3] = {1.0, 0.25, 2.0 / 3.0};
+  const double* ys = c->y;
+  for (int s = 0; s < 3; ++s) {
+    double* out = s == 0 ? c->ybuf : (s == 1 ? c->ybuf2 : c->y);
+    FusedArgs a{};
+    a.ys = ys;
+    a.out = out;
+    a.d = c->dinc;
+    a.yf = s == 2 ? c->yf : nullptr;
+    a.field = static_cast<const float*>(c->field);
+    a.list = c->list;
+    a.ctrl = c->ctrl;
+    a.b0dt = (float)(b0[s] * dt);
+    a.a0 = (float)a0[s];
+    a.stage = s + 1;
+    DG_CUDA(cudaMemsetAsync(&c->ctrl->n_flag, 0, sizeof(unsigned), c->stream));
+    DG_TRY(launch(c, KC_VOLUME, [&] { return c->fz.run(force, c->flux, c->geo, a, c->stream); }));
+    float* yf = s == 2 ? c->yf : nullptr;
+    const double* y0 = s < 2 ? c->y : nullptr;
+    float* dinc = s < 2 ? c->dinc : nullptr;
+    if (c->ind_params) {
+      DG_CUDA(cudaMemsetAsync(&c->ctrl->n_gate, 0, sizeof(unsigned), c->stream));
+      DG_TRY(launch(c, KC_LIMIT, [&] {
+        return dg::mlp::gate_for(c->k, out, c->geo, c->fn.tab64(), c->list, &c->ctrl->n_flag, c->ind_params,
+                                 c->ind_logit_thr, c->list2, &c->ctrl->n_gate, &c->ctrl->n_queued_total, c->stream);
+      }));
+      DG_TRY(launch(c, KC_LIMIT, [&] {
+        return c->fn.limit_list(out, c->list2, &c->ctrl->n_gate, c->geo, c->ctrl, 0, yf, y0, dinc, c->stream);
+      }));
+    } else {
+      DG_TRY(launch(c, KC_LIMIT, [&] {
+        return c->fn.limit_list(out, c->list, &c->ctrl->n_flag, c->geo, c->ctrl, 1, yf, y0, dinc, c->stream);
+      }));
+    }
+    ys = out;
+  }
+  c->limited = true;
+  c->shadow_valid = true;
+  return DG_OK;
 }
 
 }  // namespace
@@ -549,6 +617,7 @@ int dg_init(const dg_mesh* mesh, int order, double gamma, dg_ctx** out) {
   c->geo.eps_rho = 1e-12;
   c->geo.eps_p = 1e-12;
   c->fn = launchers_for(c->k);
+  c->fz = fused_for(c->k);
   int st = upload_tables(c->k, c->device);
   if (st != DG_OK) {
     delete c;
@@ -598,6 +667,19 @@ int dg_bind(dg_ctx* c, double* y_dev, void* scratch_dev, size_t scratch_bytes, v
   c->shadow_valid = false;
   c->ind_params = nullptr;
   c->fh = c->scratch + L.fh;
+  {
+    // the fused path's buffers inside the face-flux area (15 Q^2 x 8 bytes
+    // per cell >= 5 N x (8 + 4) bytes per cell at every degree)
+    const size_t nst = (size_t)5 * c->N * (size_t)c->geo.nc;
+    const size_t need = align256(sizeof(double) * nst) + align256(sizeof(float) * nst);
+    if (need <= L.base_end - L.fh) {
+      c->ybuf2 = reinterpret_cast<double*>(c->scratch + L.fh);
+      c->dinc = reinterpret_cast<float*>(c->scratch + L.fh + align256(sizeof(double) * nst));
+    } else {
+      c->ybuf2 = nullptr;
+      c->dinc = nullptr;
+    }
+  }
   c->field = c->forcing_capable ? c->scratch + L.field : nullptr;
   c->bound = true;
   c->limited = false;
@@ -693,6 +775,15 @@ int dg_rhs(dg_ctx* c, const double* y_dev, double* R_dev) {
   DG_TRY(set_device(c));
   const double* y = y_dev ? y_dev : c->y;
   const bool force = c->n_force > 0;
+  if (uses_fused(c)) {
+    FusedArgs a{};
+    a.ys = y;
+    a.R = R_dev;
+    a.field = static_cast<const float*>(c->field);
+    a.ctrl = c->ctrl;
+    a.stage = 0;
+    return launch(c, KC_VOLUME, [&] { return c->fz.run(force, c->flux, c->geo, a, c->stream); });
+  }
   if (uses_shadow(c) && !(y == c->y && c->shadow_valid)) {
     DG_TRY(convert_shadow(c, y));
     c->shadow_valid = y == c->y;
@@ -713,6 +804,7 @@ int dg_step(dg_ctx* c, double dt) {
     DG_TRY(launch(c, KC_LIMIT, [&] { return c->fn.limit(c->y, nullptr, c->geo, c->ctrl, c->stream); }));
     c->shadow_valid = false;
   }
+  if (uses_fused(c)) return fused_step(c, dt, force);
   const bool shadow = uses_shadow(c);
   if (shadow && !c->shadow_valid) DG_TRY(convert_shadow(c, c->y));
   float* yf = shadow ? c->yf : nullptr;
@@ -738,11 +830,12 @@ int dg_step(dg_ctx* c, double dt) {
                                  c->ind_logit_thr, c->list2, &c->ctrl->n_gate, &c->ctrl->n_queued_total, c->stream);
       }));
       DG_TRY(launch(c, KC_LIMIT, [&] {
-        return c->fn.limit_list(out, c->list2, &c->ctrl->n_gate, c->geo, c->ctrl, 0, yf, c->stream);
+        return c->fn.limit_list(out, c->list2, &c->ctrl->n_gate, c->geo, c->ctrl, 0, yf, nullptr, nullptr,
+                                c->stream);
       }));
     } else {
       DG_TRY(launch(c, KC_LIMIT, [&] {
-        return c->fn.limit_list(out, c->list, &c->ctrl->n_flag, c->geo, c->ctrl, 1, yf, c->stream);
+        return c->fn.limit_list(out, c->list, &c->ctrl->n_flag, c->geo, c->ctrl, 1, yf, nullptr, nullptr, c->stream);
       }));
     }
     ys = out;
@@ -861,7 +954,7 @@ int dg_energy_reset(dg_ctx* c, double c_iso, double rho0, double* dissipated) {
   // the positivity limiter after the reset (Sect. 3.2): full limiter on the
   // cells that failed the screen
   DG_TRY(launch(c, KC_RESET, [&] {
-    return c->fn.limit_list(c->y, c->list, &c->ctrl->n_flag, c->geo, c->ctrl, 0, yf, c->stream);
+    return c->fn.limit_list(c->y, c->list, &c->ctrl->n_flag, c->geo, c->ctrl, 0, yf, nullptr, nullptr, c->stream);
   }));
   c->limited = true;
   if (dissipated) {

@@ -225,14 +225,19 @@ __device__ __forceinline__ void hllc_flux(int d, const T* UL, const T* UR, T gam
   // aL = aR = 0. Take S* = 0; the flux is then (0, p e_d, 0), the flux at a
   // vacuum interface.
   if (aL - aR == T(0)) Ss = T(0);
+  // the side of the contact, selected by value (no pointer into either
+  // side's arrays, which would put them in local memory)
   const bool left = Ss >= T(0);
-  const T* U = left ? UL : UR;
-  const T* v = left ? vL : vR;
+  T U[5], v[3];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) U[i] = left ? UL[i] : UR[i];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) v[a] = left ? vL[a] : vR[a];
   T p = left ? pL : pR;
   T S = left ? SL : SR;
   T ak = left ? aL : aR;  // rho_K (S_K - u_K)
   T ir = left ? irL : irR;
-  T uk = v[d];
+  T uk = left ? uL : uR;
   euler_flux(d, U, v, p, F);
   // star state: chi = rho_K (S_K - u_K) / (S_K - S*), and
   // E* = chi (E_K / rho_K + (S* - u_K) (S* + p_K / (rho_K (S_K - u_K))))

@@ -200,8 +200,8 @@ cudaError_t volume_stage(int prec, bool force, const void* fh, const void* field
 }
 
 cudaError_t limit_list(double* y, const int* list, const unsigned* count, const Geo& g, Ctrl* ctrl, int count_queued,
-                       float* yf, cudaStream_t s) {
-  limit_list_kernel<KK><<<152, kThreads, 0, s>>>(y, list, count, tab_ptr<double>(), g, ctrl, count_queued, yf);
+                       float* yf, const double* y0, float* d, cudaStream_t s) {
+  limit_list_kernel<KK><<<152, kThreads, 0, s>>>(y, list, count, tab_ptr<double>(), g, ctrl, count_queued, yf, y0, d);
   return cudaGetLastError();
 }
 

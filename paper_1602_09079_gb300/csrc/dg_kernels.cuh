@@ -700,7 +700,8 @@ template <int K>
 __global__ void __launch_bounds__(kThreads) limit_list_kernel(double* __restrict__ y, const int* __restrict__ list,
                                                               const unsigned* count, const double* __restrict__ tab64,
                                                               Geo g, Ctrl* ctrl, int count_queued,
-                                                              float* __restrict__ yf) {
+                                                              float* __restrict__ yf, const double* __restrict__ y0,
+                                                              float* __restrict__ dinc) {
   constexpr int N = nmodes(K);
   const unsigned n = *count;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -710,8 +711,13 @@ __global__ void __launch_bounds__(kThreads) limit_list_kernel(double* __restrict
   unsigned e = 0;
   for (unsigned i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) {
     const long long cell = list[i];
-    if (limit_cell<K>(y + cell, g.nc, tab64, g.gamma, g.eps_rho, g.eps_p, &e, g.lim_vol) && yf)
-      for (int r = 0; r < 5 * N; ++r) yf[(size_t)r * g.nc + cell] = (float)y[(size_t)r * g.nc + cell];
+    if (limit_cell<K>(y + cell, g.nc, tab64, g.gamma, g.eps_rho, g.eps_p, &e, g.lim_vol)) {
+      if (yf)
+        for (int r = 0; r < 5 * N; ++r) yf[(size_t)r * g.nc + cell] = (float)y[(size_t)r * g.nc + cell];
+      if (dinc)
+        for (int r = 0; r < 5 * N; ++r)
+          dinc[(size_t)r * g.nc + cell] = (float)(y[(size_t)r * g.nc + cell] - y0[(size_t)r * g.nc + cell]);
+    }
   }
   if (e) atomicOr(&ctrl->err, e);
 }

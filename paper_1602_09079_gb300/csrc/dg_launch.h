@@ -32,9 +32,11 @@ struct Launchers {
                               double dt, int* list, float* yf, Ctrl* ctrl, cudaStream_t s);
   // full limiter on the *count cells of list (count_queued: also add them
   // to the screen-failure total, i.e. no indicator filtered the list); yf
-  // (nullable): FP32 shadow updated for the cells the limiter changes
+  // (nullable): FP32 shadow updated for the cells the limiter changes; d
+  // (nullable): the fused stage kernels' FP32 increment y - y0 of the step,
+  // recomputed for the cells the limiter changes
   cudaError_t (*limit_list)(double* y, const int* list, const unsigned* count, const Geo& g, Ctrl* ctrl,
-                            int count_queued, float* yf, cudaStream_t s);
+                            int count_queued, float* yf, const double* y0, float* d, cudaStream_t s);
   // screen[c] = 1 if cell c fails the limiter screen
   cudaError_t (*screen)(const double* y, uint8_t* screen, const Geo& g, cudaStream_t s);
   cudaError_t (*limit)(double* y, int8_t* flags, const Geo& g, Ctrl* ctrl, cudaStream_t s);
@@ -56,6 +58,37 @@ struct Launchers {
   const double* (*tab64)();
   size_t table_size;
 };
+
+// Fused FP32-mixed stage kernel (face fluxes, volume quadrature and stage
+// update in one launch per stage; dg_fused.cuh), built for the degrees that
+// have one; run == nullptr otherwise.
+// Arguments of one fused launch.
+struct FusedArgs {
+  const double* ys;    // stage input y^(s), state layout
+  double* out;         // stage output (must not alias ys: neighbours read ys)
+  float* d;            // FP32 increment y^(s) - y^(0): read in stages 2-3, written in 1-2
+  float* yf;           // FP32 copy of the output written in stage 3 (nullable)
+  double* R;           // stage 0: R(ys), state layout
+  const float* field;  // driving field a(x) at the volume points, [3][Q^3][nc]
+  int* list;           // cells failing the limiter screen
+  Ctrl* ctrl;
+  float b0dt, a0;      // delta = b0 dt dw/dt - a0 d
+  float eps_r, eps_p;  // positivity floors (FP32) for the limiter screen
+  int stage;           // 0: R(y); 1, 2, 3: SSP-RK3 stage
+  int lz;              // planes per z segment
+  int nbx, nby;        // tile columns along x and y
+};
+
+struct FusedLaunchers {
+  int k;
+  // 1D tables of the degree (from its FP64 table, Tab<K> layout) and the
+  // kernels' shared-memory attribute, on the current device
+  cudaError_t (*upload)(const double* h64);
+  // one launch: args.stage 0 computes R(ys), 1-3 one SSP-RK3 stage
+  cudaError_t (*run)(bool force, int flux, const Geo& g, FusedArgs& args, cudaStream_t s);
+};
+
+FusedLaunchers fused_launchers_k2();
 
 Launchers launchers_k0();
 Launchers launchers_k1();

@@ -22,11 +22,17 @@
 //       the FP32 and FP64 HLLC (or exact-Riemann) fluxes of one face point
 //
 // prec: 0 FP64, 1 mixed; flux: 0 HLLC (default), 1 exact Riemann solver.
+// Degree 2 in mixed precision runs the fused stage kernel (dg_fused.cuh) as
+// the library does; DG_EMU_FUSED=0 in the environment selects the separate
+// face and volume kernels instead.
 // States in the state layout [5][N][n_cells], FP64.
 // Prints "err=<device error word> dissipated=<...> smax=<...>".
 #include <type_traits>
 
 #include "dg_kernels.cuh"
+#if DG_K == 2
+#include "dg_fused.cuh"
+#endif
 using namespace dg;
 #include "tables.inc"
 namespace dg {
@@ -86,6 +92,53 @@ static void make_setup(Setup& S, int nx, int ny, int nz, double gamma, int lim_v
 // numerical flux: 0 HLLC, 1 exact Riemann solver (dg_set_flux)
 static int g_flux = 0;
 
+static bool use_fused() {
+#if DG_K == 2
+  const char* e = std::getenv("DG_EMU_FUSED");
+  return !(e && e[0] == '0');
+#else
+  return false;
+#endif
+}
+
+#if DG_K == 2
+// the fused kernel's 1D tables (as its upload builds them) and one launch
+// with the launcher's grid and planes per segment
+static void fused_setup(const Setup& S) {
+  using FT = FzTab<K>;
+  constexpr int KQ = (K + 1) * (K + 1);
+  for (int j = 0; j < KQ; ++j) {
+    c_fz[FT::P + j] = (float)S.t64[TB::P1 + j];
+    c_fz[FT::PW + j] = (float)S.t64[TB::P1W + j];
+    c_fz[FT::DW + j] = (float)S.t64[TB::D1W + j];
+  }
+  for (int e = 0; e <= K; ++e) {
+    c_fz[FT::EM + e] = (float)S.t64[TB::FEND + e];
+    c_fz[FT::EP + e] = (float)S.t64[TB::FEND + K + 1 + e];
+  }
+  for (int l = 0; l < TB::N; ++l) {
+    c_fz[FT::LM + l] = (float)S.t64[TB::LMAX + l];
+    c_fz[FT::LMV + l] = (float)S.t64[TB::LMAXV + l];
+  }
+}
+
+template <bool FORCE>
+static void fused_launch(Setup& S, FusedArgs a) {
+  using FC = FusedCfg<K>;
+  a.nbx = (S.g.nx + FC::BX - 1) / FC::BX;
+  a.nby = (S.g.ny + FC::BY - 1) / FC::BY;
+  // the launcher's choice for meshes that fit one wave: the smallest
+  // candidate, 4 planes per segment
+  a.lz = 4;
+  a.eps_r = (float)S.g.eps_rho;
+  a.eps_p = (float)S.g.eps_p;
+  const unsigned grid = (unsigned)(a.nbx * a.nby * ((S.g.nz + a.lz - 1) / a.lz));
+  a.ctrl = &S.ctrl;
+  if (g_flux) emu::launch(grid, FC::THREADS, FC::smem(), [&] { fused_f32_kernel<K, FORCE, 1>(S.g, a); });
+  else emu::launch(grid, FC::THREADS, FC::smem(), [&] { fused_f32_kernel<K, FORCE, 0>(S.g, a); });
+}
+#endif
+
 // face fluxes of the state ys (FP32 path: of its shadow yf)
 template <typename T, int FLUX>
 static void faces_f(Setup& S, const double* ys, float* yf, T* fh) {
@@ -131,6 +184,18 @@ static void volume(Setup& S, const double* ys, float* yf, const T* fh, const T* 
 
 template <typename T>
 static void run_rhs(Setup& S, std::vector<double>& y, std::vector<double>& R) {
+#if DG_K == 2
+  if (sizeof(T) == 4 && use_fused()) {
+    fused_setup(S);
+    FusedArgs a{};
+    a.ys = y.data();
+    a.R = R.data();
+    a.stage = 0;
+    fused_launch<false>(S, a);
+    std::printf("err=%u dissipated=0 smax=0\n", S.ctrl.err);
+    return;
+  }
+#endif
   std::vector<float> yf(sizeof(T) == 4 ? y.size() : 1);
   if (sizeof(T) == 4)
     for (size_t i = 0; i < y.size(); ++i) yf[i] = (float)y[i];  // the library's shadow: round to nearest
@@ -164,6 +229,36 @@ static void run_step(Setup& S, std::vector<double>& y, double dt, const std::vec
   std::vector<int> list(nc, -1);
   const double a0[3] = {0.0, 0.75, 1.0 / 3.0}, b0[3] = {1.0, 0.25, 2.0 / 3.0};
   const double* ys = y.data();
+#if DG_K == 2
+  if (shadow && use_fused()) {
+    // the C ABI's fused step: y -> ybuf -> ybuf2 -> y with the FP32
+    // increment of the step; the limiter recomputes it for changed cells
+    fused_setup(S);
+    std::vector<double> ybuf2(y.size(), std::nan(""));
+    std::vector<float> dinc(y.size(), std::nanf(""));
+    for (int s = 0; s < 3; ++s) {
+      double* out = s == 0 ? ybuf.data() : (s == 1 ? ybuf2.data() : y.data());
+      FusedArgs a{};
+      a.ys = ys;
+      a.out = out;
+      a.d = dinc.data();
+      a.yf = s == 2 ? yfp : nullptr;
+      a.field = reinterpret_cast<const float*>(fld);
+      a.list = list.data();
+      a.b0dt = (float)(b0[s] * dt);
+      a.a0 = (float)a0[s];
+      a.stage = s + 1;
+      S.ctrl.n_flag = 0;
+      if (force) fused_launch<true>(S, a);
+      else fused_launch<false>(S, a);
+      emu::launch(152, kThreads, 0, [&] {
+        limit_list_kernel<K>(out, list.data(), &S.ctrl.n_flag, S.t64.data(), S.g, &S.ctrl, 1, s == 2 ? yfp : nullptr,
+                             s < 2 ? y.data() : nullptr, s < 2 ? dinc.data() : nullptr);
+      });
+      ys = out;
+    }
+  } else
+#endif
   for (int s = 0; s < 3; ++s) {
     double* out = s < 2 ? ybuf.data() : y.data();
     faces<T>(S, ys, yfp, fh.data());
@@ -172,7 +267,7 @@ static void run_step(Setup& S, std::vector<double>& y, double dt, const std::vec
     if (force) volume<T, MODE_STAGE, true>(S, ys, yfp, fh.data(), fld, st, nullptr);
     else volume<T, MODE_STAGE, false>(S, ys, yfp, fh.data(), fld, st, nullptr);
     emu::launch(152, kThreads, 0, [&] {
-      limit_list_kernel<K>(out, list.data(), &S.ctrl.n_flag, S.t64.data(), S.g, &S.ctrl, 1, yfp);
+      limit_list_kernel<K>(out, list.data(), &S.ctrl.n_flag, S.t64.data(), S.g, &S.ctrl, 1, yfp, nullptr, nullptr);
     });
     ys = out;
   }
@@ -190,7 +285,7 @@ static void run_step(Setup& S, std::vector<double>& y, double dt, const std::vec
     energy_reset_kernel<K, T, 32>(y.data(), tabT, S.t64.data(), S.g, rc, part.data(), list.data(), &S.ctrl, yfp);
   });
   emu::launch(152, kThreads, 0, [&] {
-    limit_list_kernel<K>(y.data(), list.data(), &S.ctrl.n_flag, S.t64.data(), S.g, &S.ctrl, 0, yfp);
+    limit_list_kernel<K>(y.data(), list.data(), &S.ctrl.n_flag, S.t64.data(), S.g, &S.ctrl, 0, yfp, nullptr, nullptr);
   });
   double diss = 0.0;
   for (unsigned b = 0; b < nbr; ++b) diss += part[b];

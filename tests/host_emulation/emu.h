@@ -210,6 +210,11 @@ struct uint4 {
 };
 inline uint4 make_uint4(unsigned x, unsigned y, unsigned z, unsigned w) { return {x, y, z, w}; }
 inline float __expf(float x) { return std::exp(x); }
+inline float __fdividef(float a, float b) { return a / b; }
+// hi:lo shifted left by s mod 32, upper 32 bits
+inline unsigned __funnelshift_l(unsigned lo, unsigned hi, unsigned s) {
+  return (unsigned)(((((unsigned long long)hi << 32) | lo) << (s & 31)) >> 32);
+}
 
 namespace emu {
 // mma.sync m16n8k16 row.col, BF16 inputs, FP32 accumulate, over the warp:
@@ -250,6 +255,8 @@ inline void mma_bf16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[
 inline double rsqrt(double x) { return 1.0 / std::sqrt(x); }
 inline float rsqrtf(float x) { return 1.0f / std::sqrt(x); }
 using std::cbrt;
+using std::max;
+using std::min;
 using std::fmax;
 using std::fmin;
 using std::isfinite;

@@ -46,7 +46,7 @@ def _host_smem(src):
 def _generate(dst):
     """The kernel headers with host dynamic shared memory, the table builder
     of dg_api.cu and the analysis kernels of dg_spectrum.cu."""
-    for f in ("dg_common.cuh", "dg_kernels.cuh"):
+    for f in ("dg_common.cuh", "dg_kernels.cuh", "dg_fused.cuh", "dg_launch.h"):
         open(os.path.join(dst, f), "w").write(_host_smem(open(os.path.join(CSRC, f)).read()))
     api = open(os.path.join(CSRC, "dg_api.cu")).read()
     a = api.index("// ----------------------------------------------------------------- tables")
