@@ -55,7 +55,9 @@ def parse():
     ap.add_argument("--flux", choices=["hllc", "exact"], default="hllc",
                     help="numerical flux: HLLC or the exact Riemann solver")
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--err-steps", type=int, default=10)
+    ap.add_argument("--err-steps", type=int, default=None,
+                    help="steps of the untimed mixed-vs-FP64 error run at a fixed dt (default: the "
+                         "configurations' lengths, 200 at order 3 and 100 at order 4)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--sweep", action="store_true",
@@ -207,26 +209,33 @@ def roofline_entry(kind, achieved, peak, unit, bound, traffic=None):
             "frac": (achieved / peak) if peak else None, "traffic": traffic}
 
 
-def step_roofline(k, mixed, nc, ms_per_step, hbm_gbs, fp64_peak=1.25e12):
-    """Whole-step roofline: algorithmic HBM bytes of one step (CFL, three
-    stages of faces and volume, energy reset; roofline.step_bytes) over the
-    measured step time against the measured HBM bandwidth, and for the FP64
-    path also the algorithmic FP64 flops of its face and volume kernels
-    against the FP64 peak (that path's bound)."""
+def step_roofline(k, mixed, nc, ms_per_step, hbm_gbs):
+    """Whole-step roofline: the algorithmic work of the step's three RK
+    stages (roofline.step_min_bytes: read y_s, y_0, write y_{s+1} in FP64;
+    3 x roofline.stage_flops, sum-factorised) plus the energy reset (read the
+    density and momentum modes and the energy mean, write the energy modes)
+    and the CFL reduction (five means), over the measured step time; bound
+    by the larger of the ALU time (FP32 peak on the mixed path, FP64 on the
+    plain one) and the HBM time."""
     from paper_1602_09079_gb300 import roofline as rl
+    N = (k + 1) * (k + 2) * (k + 3) // 6
     sec = ms_per_step * 1e-3
-    byts = rl.step_bytes(k, mixed) * nc
-    gbs = byts / sec / 1e9
-    out = {"bound": "hbm", "achieved": gbs, "peak": hbm_gbs, "unit": "GB/s",
-           "frac": gbs / hbm_gbs if hbm_gbs else None, "bytes_per_step": byts,
-           "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
-    if not mixed:
-        vol = rl.volume_sf_flops(k, True) if k >= 2 else rl.volume_flops(k, True)
-        flops = 3 * (rl.face_sf_flops(k) + vol) * nc
-        out.update({"bound": "alu", "achieved": flops / sec / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
-                    "frac": flops / sec / fp64_peak, "flops_per_step": flops, "hbm_gbs": gbs,
-                    "hbm_frac": gbs / hbm_gbs if hbm_gbs else None,
-                    "peak_source": "derived: FP64 1.25 TFLOP/s datasheet"})
+    byts = (rl.step_min_bytes(k) + (4 * N + 1 + N) * 8 + 5 * 8) * nc
+    flops = 3 * rl.stage_flops(k, True) * nc
+    peak = rl.FP32_PEAK if mixed else rl.FP64_PEAK
+    t_alu = flops / peak
+    t_hbm = byts / (hbm_gbs * 1e9) if hbm_gbs else None
+    out = {"bytes_per_step": byts, "flops_per_step": flops, "achieved_gbs": byts / sec / 1e9,
+           "achieved_tflops": flops / sec / 1e12, "peak_source": rl.PEAK_SOURCE,
+           "impl_bytes_per_step": rl.step_bytes(k, mixed) * nc}
+    if t_hbm is None:
+        out.update({"bound": None, "achieved": None, "peak": None, "unit": None, "frac": None})
+    elif t_alu >= t_hbm:
+        out.update({"bound": "alu", "achieved": flops / sec / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+                    "frac": t_alu / sec})
+    else:
+        out.update({"bound": "hbm", "achieved": byts / sec / 1e9, "peak": hbm_gbs, "unit": "GB/s",
+                    "frac": t_hbm / sec})
     return out
 
 
@@ -364,47 +373,39 @@ def run_ours(args):
     hbm = peaks.get("hbm_gbs")
     fp64_probe = dgm.dg_probe_fma_peak(True)
     fp32_probe = dgm.dg_probe_fma_peak(False)
-    # derived ALU peaks: 152 SMs x lanes x 2 flops x 2.07 GHz (FP32: 128 lanes);
-    # FP64 1.25 TFLOP/s (GB300 datasheet figure)
-    fp32_peak = 152 * 128 * 2 * 2.07e9
-    fp64_peak = 1.25e12
 
     def kernel_roofline(prec_name, tsize):
+        """Roofline of one RK stage: the stage kernels' time per
+        stage (the fused kernel on the mixed path at degree 2; face and volume
+        kernels otherwise) against the algorithmic bytes and flops of a stage
+        (roofline.stage_roofline); traffic = the ncu DRAM bytes of the timed
+        kernel per launch, with its ratio to the algorithmic bytes."""
         kst = results[prec_name]["ktimes"]
         nvol, msvol = kst["volume"]
-        per_launch_s = msvol / nvol * 1e-3
-        sumfact = k >= 2 and not (tsize == 4 and k <= 2)
-        flops = (rl.volume_sf_flops(k, True) if sumfact else rl.volume_flops(k, True)) * nc
-        # the FP32 stage kernels skip y_0 in the first stage (a0 = 0): the
-        # algorithmic bytes per launch are the average over the three stages
-        if tsize == 4:
-            byts = (rl.volume_bytes(k, tsize, True, reads_y0=False, shadow=True)
-                    + 2 * rl.volume_bytes(k, tsize, True, shadow=True)) / 3 * nc
+        nface, msface = kst["face_flux"]
+        stage_ms = (msvol + msface) / nvol
+        peak = rl.FP32_PEAK if tsize == 4 else rl.FP64_PEAK
+        e = rl.stage_roofline(k, True, nc, stage_ms, hbm, peak)
+        e["peak_source"] = rl.PEAK_SOURCE
+        fused = tsize == 4 and nface == 0
+        if fused:
+            kname = f"fused_f32_kernel<{k}, true, 0>"
+            e["kernel"] = kname + " (stage, forcing; face fluxes, volume integral and stage update in one launch)"
+            e["impl_bytes_per_launch"] = rl.fused_impl_bytes(k, True) * nc
         else:
-            byts = rl.volume_bytes(k, tsize, True) * nc
-        t_alu = flops / (fp64_peak if tsize == 8 else fp32_peak)
-        t_hbm = byts / (hbm * 1e9) if hbm else 0.0
-        if t_alu >= t_hbm:
-            e = roofline_entry("alu", flops / per_launch_s / 1e12, (fp64_peak if tsize == 8 else fp32_peak) / 1e12,
-                               "TFLOP/s", "alu")
-            e["peak_source"] = ("derived: FP64 1.25 TFLOP/s datasheet" if tsize == 8 else
-                                "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz")
-        else:
-            e = roofline_entry("hbm", byts / per_launch_s / 1e9, hbm, "GB/s", "hbm")
-            e["peak_source"] = "measured (MEASURED_PEAKS.json hbm_gbs)"
-        kname = (f"volume_f32_kernel<{k}, 1, 1>" if (tsize == 4 and k <= 2)
-                 else f"volume_{('sfb_' if tsize == 4 else 'sf_') if sumfact else ''}kernel<{k}, "
-                 f"{'double' if tsize == 8 else 'float'}, 1, 1>")
-        e["kernel"] = kname + " (stage, forcing)"
+            sumfact = k >= 2
+            kname = (f"volume_f32_kernel<{k}, 1, 1>" if (tsize == 4 and k <= 2)
+                     else f"volume_{('sfb_' if tsize == 4 else 'sf_') if sumfact else ''}kernel<{k}, "
+                     f"{'double' if tsize == 8 else 'float'}, 1, 1>")
+            e["kernel"] = kname + " (stage, forcing) + its face kernel"
+            e["impl_bytes_per_launch"] = (rl.volume_bytes(k, tsize, True, shadow=tsize == 4)
+                                          + rl.face_bytes(k, tsize)) * nc
         tr = ncu_traffic().get(kname)
-        if tr:
+        e["traffic"] = None
+        if tr and not tr.get("stale"):
             e["traffic"] = tr["dram_bytes_per_cell"] * nc
             e["traffic_source"] = tr.get("source")
-        e["flops_per_launch"] = flops
-        e["bytes_per_launch"] = byts
-        e["ms_per_launch"] = per_launch_s * 1e3
-        e["achieved_gbs"] = byts / per_launch_s / 1e9
-        e["achieved_tflops"] = flops / per_launch_s / 1e12
+            e["traffic_over_algorithmic_bytes"] = e["traffic"] / e["bytes_per_launch"]
         tot = sum(v[1] for v in kst.values())
         e["share_of_step"] = {kk: (v[1] / tot if tot else None) for kk, v in kst.items()}
         e["ms_per_launch_by_class"] = {kk: (v[1] / v[0] if v[0] else None) for kk, v in kst.items()}
@@ -583,6 +584,8 @@ def run_sweep(args):
 
 def main():
     args = parse()
+    if args.err_steps is None:
+        args.err_steps = 200 if args.order <= 3 else 100
     if args.sweep:
         run_sweep(args)
         return

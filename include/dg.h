@@ -311,8 +311,7 @@ int dg_indicator_adam(float* params, float* m, float* v, const float* grads, int
                       float beta1, float beta2, float eps, int step, void* cuda_stream);
 
 /* ---- allocation-free entry point (no counterpart in the paper) ---------
- * R(y) exactly as dg_rhs computes it (same kernels; HLLC flux, no driving
- * source), for
+ * R(y) as dg_rhs computes it (no driving source), for
  * callers that must not allocate device memory themselves: code whose device
  * memory is owned and budgeted by a host application or another framework's
  * allocator, where a cudaMalloc (or the implicit synchronisation of a
@@ -333,7 +332,15 @@ int dg_indicator_adam(float* params, float* m, float* v, const float* grads, int
  * capture. All calls share the one array: calls that overlap on the GPU (on
  * different streams, or from several threads) race on it; serialise them.
  * The array keeps the last call's contents; every entry a call reads is
- * written by the same call first. */
+ * written by the same call first, and each call clears the array's control
+ * block (error bits) on the stream before its kernels run.
+ * The numerical flux is always HLLC (there is no context, so dg_set_flux
+ * does not apply). FP64: the kernels of dg_rhs, same results. DG_PREC_MIXED:
+ * the separate FP32 face and volume kernels, within FP32 rounding of
+ * dg_rhs (which runs the fused stage kernel at degree 2).
+ * Device-side errors are not reported: a non-finite y gives a non-finite R
+ * and DG_OK, so check R where that matters; the return value covers the
+ * arguments, the size limit and CUDA launch errors only. */
 #define DG_NOALLOC_SCRATCH_BYTES (32u << 20)
 int dg_rhs_noalloc(const dg_mesh* mesh, int order, double gamma, int precision, const double* y_dev,
                    double* R_dev, void* cuda_stream);

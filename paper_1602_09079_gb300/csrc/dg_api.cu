@@ -371,6 +371,7 @@ struct dg_ctx {
   bool limited = false;
   int n_force = 0;
   std::vector<double> modes_host;  // 9 per mode
+  dg::spec::PlanCache fft;         // cuFFT plan of the velocity spectrum
 };
 
 namespace {
@@ -592,9 +593,11 @@ int dg_init(const dg_mesh* mesh, int order, double gamma, dg_ctx** out) {
   long long nc = 1;
   for (int a = 0; a < 3; ++a) {
     if (mesh->n[a] < 1 || !(mesh->length[a] > 0.0) || !std::isfinite(mesh->length[a])) return DG_ERR_ARG;
+    // cell counts stay below 2^31 (32-bit cell indices): checked before each
+    // product, so the product itself cannot overflow
+    if (nc > ((1LL << 31) - 1) / mesh->n[a]) return DG_ERR_ARG;
     nc *= mesh->n[a];
   }
-  if (nc > (1LL << 31) - 1) return DG_ERR_ARG;
   dg_ctx* c = new (std::nothrow) dg_ctx();
   if (!c) return DG_ERR_ARG;
   c->k = order - 1;
@@ -629,6 +632,7 @@ int dg_init(const dg_mesh* mesh, int order, double gamma, dg_ctx** out) {
 
 void dg_destroy(dg_ctx* c) {
   if (!c) return;
+  if (c->fft.M && cudaSetDevice(c->device) == cudaSuccess) dg::spec::release(&c->fft);
   for (auto& p : c->pending) {
     cudaEventDestroy(p.a);
     cudaEventDestroy(p.b);
@@ -1015,7 +1019,7 @@ int dg_spectrum_sizes(const dg_ctx* c, int sub, size_t* work_bytes, int* n_bins)
   DG_TRY(spectrum_args(c, sub, &M));
   if (!work_bytes || !n_bins) return DG_ERR_ARG;
   DG_TRY(set_device(c));
-  const size_t b = dg::spec::work_bytes(M);
+  const size_t b = dg::spec::work_bytes(M, const_cast<dg::spec::PlanCache*>(&c->fft));
   if (b == 0) return DG_ERR_TOO_LARGE;
   *work_bytes = b;
   *n_bins = dg::spec::n_bins(M);
@@ -1029,7 +1033,8 @@ int dg_velocity_spectrum(dg_ctx* c, int sub, void* work_dev, size_t work_bytes, 
   if (!work_dev || !spectrum) return DG_ERR_ARG;
   DG_TRY(set_device(c));
   int cst = 0;
-  DG_CUDA(dg::spec::velocity_spectrum(c->k, c->y, c->geo.nx, sub, work_dev, work_bytes, spectrum, c->stream, &cst));
+  DG_CUDA(dg::spec::velocity_spectrum(c->k, c->y, c->geo.nx, sub, work_dev, work_bytes, spectrum, c->stream, &cst,
+                                      &c->fft));
   if (cst == -1) return DG_ERR_ARG;
   if (cst != 0) return DG_ERR_CUDA;
   return DG_OK;
@@ -1294,6 +1299,8 @@ extern "C" int dg_rhs_noalloc(const dg_mesh* mesh, int order, double gamma, int 
   long long nc = 1;
   for (int a = 0; a < 3; ++a) {
     if (mesh->n[a] < 1 || !(mesh->length[a] > 0.0) || !std::isfinite(mesh->length[a])) return DG_ERR_ARG;
+    // bounded before each product (as in dg_init), so it cannot overflow
+    if (nc > ((1LL << 31) - 1) / mesh->n[a]) return DG_ERR_ARG;
     nc *= mesh->n[a];
     g.dx[a] = mesh->length[a] / mesh->n[a];
     g.inv_dx[a] = 1.0 / g.dx[a];
@@ -1302,7 +1309,7 @@ extern "C" int dg_rhs_noalloc(const dg_mesh* mesh, int order, double gamma, int 
   const size_t tsize = precision == DG_PREC_MIXED ? sizeof(float) : sizeof(double);
   const size_t ctrl_bytes = 256;
   const Launchers L = launchers_for(k);
-  // FP32 path of degrees <= 2: an FP32 copy of y sits behind the face fluxes
+  // FP32 path (every degree): an FP32 copy of y sits behind the face fluxes
   const bool shadow = precision == DG_PREC_MIXED && L.f32_shadow;
   const size_t per_cell = (size_t)15 * Q * Q * tsize + (shadow ? (size_t)5 * nmodes(k) * sizeof(float) : 0);
   if (nc > (long long)(kNoAllocBytes / per_cell) || ctrl_bytes + per_cell * (size_t)nc + 256 > kNoAllocBytes)
@@ -1322,6 +1329,11 @@ extern "C" int dg_rhs_noalloc(const dg_mesh* mesh, int order, double gamma, int 
   void* fh = static_cast<unsigned char*>(scratch) + ctrl_bytes;
   float* yf = nullptr;
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  // the kernels OR sticky error bits into the control block at the start of
+  // the array; clear it on the stream first (a memset allocates nothing), so
+  // nothing a previous call left there carries over. No call reads it back:
+  // this entry point reports no device-side errors.
+  DG_CUDA(cudaMemsetAsync(ctrl, 0, ctrl_bytes, s));
   if (shadow) {
     const size_t fh_bytes = (size_t)15 * Q * Q * tsize * (size_t)nc;
     yf = reinterpret_cast<float*>(static_cast<unsigned char*>(fh) + ((fh_bytes + 255) & ~size_t(255)));

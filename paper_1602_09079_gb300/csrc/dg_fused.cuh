@@ -11,11 +11,13 @@
 //      traces of the column's outer x and y faces;
 //  P2  one numerical flux per face point (x, y faces of the plane, and the
 //      z face between the previous plane and this one), scaled by 1/(4 dx);
-//  P3  each face's flux is projected onto both cells that share it (the z
-//      face also completes the previous plane's cells);
-//  P4  the previous plane's cells are finished: R, or the stage update
-//      y_{s+1} = y_s + delta with delta = b0 dt dw/dt - a0 d (FP32) added in
-//      FP64, d = y_s - y_0 the FP32 increment of the step so far;
+//  P3  the z face between the previous plane and this one completes the
+//      previous plane's cells, then
+//  P4  finishes them: R, or the stage update y_{s+1} = y_s + delta with
+//      delta = b0 dt dw/dt - a0 d (FP32) added in FP64, d = y_s - y_0 the
+//      FP32 increment of the step so far; each thread's accumulators then
+//      restart with this plane's low z face and its x and y faces (every
+//      face's flux is projected onto both cells that share it);
 //  P5  the limiter screen of those cells (sufficient test in FP32 with a
 //      1e-5 relative margin; failing cells are queued for the full FP64
 //      limiter);
@@ -378,12 +380,9 @@ __global__ void __launch_bounds__(FusedCfg<K>::THREADS, FusedCfg<K>::MINB) fused
   const int rfvx = face_var(0, riv), rfvy = face_var(1, riv);
   const float eps_r = a.eps_r, eps_p = a.eps_p;
 
-  float w[N], acc[N], accp[N];
+  float w[N], acc[N];
 #pragma unroll
-  for (int l = 0; l < N; ++l) {
-    acc[l] = 0.f;
-    accp[l] = 0.f;
-  }
+  for (int l = 0; l < N; ++l) acc[l] = 0.f;
 
   for (int pz = -1; pz <= vz; ++pz) {
     int zc = z0 + pz;
@@ -456,11 +455,51 @@ __global__ void __launch_bounds__(FusedCfg<K>::THREADS, FusedCfg<K>::MINB) fused
       }
     }
     __syncthreads();
-    // ---------------------------------------------------------------- P3
+    // ------------------------------------------------------------ P3, P4
+    // On entry acc holds the previous plane's dw/dt without its high z
+    // face. The z face closes it (P4: R or the stage update), then acc
+    // restarts with this plane's low z face and its x and y faces.
     if (cval) {
+      float H[T];
+      if (pz >= 0) fz_moments<K>(sm + CF::ZR + fvz * Q2 * SZ + c, SZ, H);
+      if (pz >= 1) {
+#pragma unroll
+        for (int aa = 0, j = 0; aa <= K; ++aa)
+#pragma unroll
+          for (int b = 0; aa + b <= K; ++b, ++j)
+#pragma unroll
+            for (int e = 0; e + aa + b <= K; ++e) {
+              const int m = face_mode<2>(e, aa, b);
+              acc[m] = fmaf(-c_fz[TB::EP + e], H[j], acc[m]);
+            }
+        const size_t o0 = (size_t)(i * N) * rs + (size_t)(zprev + cxy);
+        if (a.stage == 0) {
+          double* pr = a.R + o0;
+#pragma unroll
+          for (int l = 0; l < N; ++l, pr += rs) *pr = f32_to_f64_q(-acc[l]);
+        } else {
+          float sab = 0.f;
+          double mean = 0.0;
+          size_t o = o0;
+#pragma unroll
+          for (int l = 0; l < N; ++l, o += rs) {
+            const double ysv = __ldg(a.ys + o);
+            const float dl = a.stage >= 2 ? a.d[o] : 0.f;
+            const float delta = fmaf(a.b0dt, acc[l], -a.a0 * dl);
+            const double v = ysv + f32_to_f64_q(delta);
+            a.out[o] = v;
+            if (a.stage <= 2) a.d[o] = dl + delta;
+            else if (a.yf) a.yf[o] = f64_to_f32_q(v);
+            if (l == 0) mean = v;
+            else sab = fmaf(abs_up(v), c_fz[(g.lim_vol ? TB::LMV : TB::LM) + l], sab);
+          }
+          sm[CF::SMN + i * NC + c] = f64_to_f32_q(mean);
+          sm[CF::SAB + i * NC + c] = sab * (1.f + 1e-5f);
+        }
+      }
+#pragma unroll
+      for (int l = 0; l < N; ++l) acc[l] = 0.f;
       if (pz >= 0) {
-        float H[T];
-        fz_moments<K>(sm + CF::ZR + fvz * Q2 * SZ + c, SZ, H);
 #pragma unroll
         for (int aa = 0, j = 0; aa <= K; ++aa)
 #pragma unroll
@@ -469,7 +508,6 @@ __global__ void __launch_bounds__(FusedCfg<K>::THREADS, FusedCfg<K>::MINB) fused
             for (int e = 0; e + aa + b <= K; ++e) {
               const int m = face_mode<2>(e, aa, b);
               acc[m] = fmaf(c_fz[TB::EM + e], H[j], acc[m]);
-              accp[m] = fmaf(-c_fz[TB::EP + e], H[j], accp[m]);
             }
       }
       if (own) {
@@ -484,36 +522,6 @@ __global__ void __launch_bounds__(FusedCfg<K>::THREADS, FusedCfg<K>::MINB) fused
       // high-z traces of this plane for the next plane's z faces (the
       // previous ones were consumed in P2)
       if (pz < vz) fz_trace<K, 2, 1>(w, sm + CF::ZL + fvz * Q2 * SZ + c, SZ);
-    }
-    // ---------------------------------------------------------------- P4
-    if (pz >= 1 && cval) {
-      const size_t o0 = (size_t)(i * N) * rs + (size_t)(zprev + cxy);
-      if (a.stage == 0) {
-        double* pr = a.R + o0;
-#pragma unroll
-        for (int l = 0; l < N; ++l) {
-          *pr = f32_to_f64_q(-accp[l]);
-          pr += rs;
-        }
-      } else {
-        float sab = 0.f;
-        double mean = 0.0;
-        size_t o = o0;
-#pragma unroll
-        for (int l = 0; l < N; ++l, o += rs) {
-          const double ysv = __ldg(a.ys + o);
-          const float dl = a.stage >= 2 ? a.d[o] : 0.f;
-          const float delta = fmaf(a.b0dt, accp[l], -a.a0 * dl);
-          const double v = ysv + f32_to_f64_q(delta);
-          a.out[o] = v;
-          if (a.stage <= 2) a.d[o] = dl + delta;
-          else if (a.yf) a.yf[o] = f64_to_f32_q(v);
-          if (l == 0) mean = v;
-          else sab = fmaf(abs_up(v), c_fz[(g.lim_vol ? TB::LMV : TB::LM) + l], sab);
-        }
-        sm[CF::SMN + i * NC + c] = f64_to_f32_q(mean);
-        sm[CF::SAB + i * NC + c] = sab * (1.f + 1e-5f);
-      }
     }
     __syncthreads();
     // ---------------------------------------------------------------- P5
@@ -695,11 +703,6 @@ __global__ void __launch_bounds__(FusedCfg<K>::THREADS, FusedCfg<K>::MINB) fused
       }
     }
     __syncthreads();
-#pragma unroll
-    for (int l = 0; l < N; ++l) {
-      accp[l] = acc[l];
-      acc[l] = 0.f;
-    }
   }
   if (err) atomicOr(&a.ctrl->err, err);
 }

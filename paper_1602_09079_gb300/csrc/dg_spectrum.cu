@@ -149,35 +149,53 @@ cudaError_t density_pdf(int k, const double* y, int n, int sub, double lo, doubl
 
 int n_bins(int M) { return (int)std::floor(std::sqrt(3.0) * M / 2.0) + 2; }
 
-size_t work_bytes(int M) {
+void release(PlanCache* cache) {
+  if (cache->M) cufftDestroy((cufftHandle)cache->handle);
+  cache->M = 0;
+  cache->ws = 0;
+}
+
+// the cached plan for M points per axis, made if the cache holds another
+// size or none
+static cufftResult cached_plan(int M, PlanCache* cache) {
+  if (cache->M == M) return CUFFT_SUCCESS;
+  release(cache);
   cufftHandle plan;
   size_t ws = 0;
-  if (make_plan(M, &plan, &ws) != CUFFT_SUCCESS) return 0;
-  cufftDestroy(plan);
+  const cufftResult r = make_plan(M, &plan, &ws);
+  if (r != CUFFT_SUCCESS) return r;
+  cache->handle = (int)plan;
+  cache->M = M;
+  cache->ws = ws;
+  return CUFFT_SUCCESS;
+}
+
+size_t work_bytes(int M, PlanCache* cache) {
+  if (cached_plan(M, cache) != CUFFT_SUCCESS) return 0;
+  const size_t ws = cache->ws;
   const size_t M3 = (size_t)M * M * M, half = (size_t)M * M * (M / 2 + 1);
   return align256(sizeof(double) * n_bins(M)) + align256(sizeof(double) * M3) + align256(sizeof(double2) * half) +
          align256(ws);
 }
 
 cudaError_t velocity_spectrum(int k, const double* y, int n, int sub, void* work, size_t bytes, double* bins_out,
-                              cudaStream_t s, int* cufft_status) {
+                              cudaStream_t s, int* cufft_status, PlanCache* cache) {
   *cufft_status = 0;
   const int M = n * sub, nb = n_bins(M);
   const size_t M3 = (size_t)M * M * M, half = (size_t)M * M * (M / 2 + 1);
-  cufftHandle plan;
-  size_t ws = 0;
-  cufftResult r = make_plan(M, &plan, &ws);
+  cufftResult r = cached_plan(M, cache);
   if (r != CUFFT_SUCCESS) {
     *cufft_status = (int)r;
     return cudaSuccess;
   }
+  const cufftHandle plan = (cufftHandle)cache->handle;
+  const size_t ws = cache->ws;
   unsigned char* p = static_cast<unsigned char*>(work);
   double* bins = reinterpret_cast<double*>(p);
   double* real = reinterpret_cast<double*>(p + align256(sizeof(double) * nb));
   double2* cplx = reinterpret_cast<double2*>(reinterpret_cast<unsigned char*>(real) + align256(sizeof(double) * M3));
   void* area = reinterpret_cast<unsigned char*>(cplx) + align256(sizeof(double2) * half);
   if (static_cast<unsigned char*>(area) + ws > p + bytes) {
-    cufftDestroy(plan);
     *cufft_status = -1;
     return cudaSuccess;
   }
@@ -194,7 +212,6 @@ cudaError_t velocity_spectrum(int k, const double* y, int n, int sub, void* work
   if (r == CUFFT_SUCCESS && e == cudaSuccess)
     e = cudaMemcpyAsync(bins_out, bins, sizeof(double) * nb, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  cufftDestroy(plan);
   if (r != CUFFT_SUCCESS) *cufft_status = (int)r;
   return e;
 }

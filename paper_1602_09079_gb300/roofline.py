@@ -27,7 +27,18 @@ volume_kernel (dense quadrature; the FP32 tiled kernel follows the same counts)
     stage combination     5 N x 5                  (RK stage only)
     limiter screen        ~ 10 N + 30              (RK stage only)
 
-Algorithmic HBM bytes (unique data each launch must touch):
+Algorithmic roofline of one RK stage (the method's own work, whatever
+form a kernel takes): read y_s, read y_0 (stages 2-3), write y_{s+1}, FP64,
+on average 8/3 x 5 N x 8 bytes per cell (stage_min_bytes); the
+sum-factorised volume and face flop counts (stage_flops). The fused
+FP32-mixed stage kernel's own traffic (fused_impl_bytes) reads y_s and the
+FP32 increment d instead of y_0, and the cached driving field.
+
+Peaks: HBM from MEASURED_PEAKS.json; FP32 152 SMs x 128 FMA lanes x 2
+flops x 2.07 GHz (unit counts and maximum clock of the GB300); FP64 the
+GB300's nominal 1.25 TFLOP/s.
+
+Kernel bytes (unique data each launch must touch):
     face:   read y_s (5 N x 8) + write face fluxes (15 Q2 x sizeof(T))
     volume: read y_s, y_0 (stages 2-3), face fluxes, forcing field
             (3 Q3 x sizeof(T)), write y_{s+1} (5 N x 8 each); the FP32 stage
@@ -140,3 +151,58 @@ def step_min_bytes(k):
     y_s, read y_0 on stages 2-3, write y_{s+1} (FP64 state)."""
     N = (k + 1) * (k + 2) * (k + 3) // 6
     return (3 + 2 + 3) * 5 * N * 8
+
+
+FP32_PEAK = 152 * 128 * 2 * 2.07e9
+FP64_PEAK = 1.25e12
+PEAK_SOURCE = ("HBM: MEASURED_PEAKS.json hbm_gbs (measured copy); FP32: 152 SM x 128 lanes x 2 flops x "
+               "2.07 GHz (unit counts, maximum clock); FP64: nominal 1.25 TFLOP/s of the GB300")
+
+
+def stage_min_bytes(k):
+    """Algorithmic HBM bytes per cell of one RK stage, averaged over the
+    three stages: read y_s, y_0 (stages 2-3), write y_{s+1} in FP64."""
+    return step_min_bytes(k) / 3
+
+
+def stage_flops(k, forcing):
+    """Algorithmic flops per cell of one RK stage: the sum-factorised volume
+    integral (with the driving source when forcing) and the three faces a
+    cell owns, traces and numerical flux included."""
+    return volume_sf_flops(k, forcing) + face_sf_flops(k)
+
+
+def fused_impl_bytes(k, forcing):
+    """HBM bytes per cell the fused FP32-mixed stage kernel moves, averaged
+    over the three stages: every stage reads y_s (FP64) and the driving
+    field (FP32) and writes y_{s+1} (FP64); stages 1-2 write the FP32
+    increment d, stages 2-3 read it; stage 3 writes the FP32 shadow.
+    Neighbour coefficients are re-read from L2 and not counted."""
+    N, Q, Q2, Q3 = _dims(k)
+    st, f32 = 5 * N * 8, 5 * N * 4
+    fld = 3 * Q3 * 4 if forcing else 0
+    s1 = st + fld + st + f32
+    s2 = st + f32 + fld + st + f32
+    s3 = st + f32 + fld + st + f32
+    return (s1 + s2 + s3) / 3
+
+
+def stage_roofline(k, forcing, nc, stage_ms, hbm_gbs, fp_peak):
+    """Roofline entry of one RK stage: the larger of the algorithmic flops
+    over the ALU peak and the algorithmic bytes over the HBM peak is the
+    bound; achieved = that quantity over the measured stage time."""
+    sec = stage_ms * 1e-3
+    flops = stage_flops(k, forcing) * nc
+    byts = stage_min_bytes(k) * nc
+    t_alu = flops / fp_peak
+    t_hbm = byts / (hbm_gbs * 1e9) if hbm_gbs else 0.0
+    out = {"flops_per_launch": flops, "bytes_per_launch": byts, "ms_per_launch": stage_ms,
+           "achieved_tflops": flops / sec / 1e12, "achieved_gbs": byts / sec / 1e9,
+           "roofline_ms": max(t_alu, t_hbm) * 1e3}
+    if t_alu >= t_hbm:
+        out.update({"bound": "alu", "achieved": flops / sec / 1e12, "peak": fp_peak / 1e12, "unit": "TFLOP/s",
+                    "frac": t_alu / sec})
+    else:
+        out.update({"bound": "hbm", "achieved": byts / sec / 1e9, "peak": hbm_gbs, "unit": "GB/s",
+                    "frac": t_hbm / sec})
+    return out

@@ -85,6 +85,19 @@ def test_init_rejects_null_pointers_and_huge_meshes(lib):
     assert lib.dg_init(C.byref(big), 3, 1.4, C.byref(out)) == dg.DG_ERR_ARG
 
 
+def test_cell_count_overflow_is_an_argument_error(lib):
+    """Three axes whose product wraps a 64-bit count to 0 (2^21 x 2^21 x
+    2^22 = 2^64): rejected before the product is formed, by dg_init and by
+    dg_rhs_noalloc, without touching the device."""
+    out = C.c_void_p()
+    p = C.c_void_p(16)
+    for n in [(1 << 21, 1 << 21, 1 << 22), (1 << 30, 4, 1), (65536, 65536, 2)]:
+        m = _mesh(n)
+        assert lib.dg_init(C.byref(m), 3, 1.4, C.byref(out)) == dg.DG_ERR_ARG, n
+        assert out.value is None
+        assert lib.dg_rhs_noalloc(C.byref(m), 3, 1.4, dg.DG_PREC_FP64, p, p, None) == dg.DG_ERR_ARG, n
+
+
 def test_noalloc_argument_and_size_errors(lib):
     m = _mesh((8, 8, 8))
     p = C.c_void_p(16)

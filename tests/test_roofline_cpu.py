@@ -35,14 +35,45 @@ def test_fp64_step_bytes_by_hand():
         assert rl.step_bytes(k, False) == 40 + faces + vol + reset
 
 
+def test_stage_algorithmic_counts_by_hand():
+    """read y_s, y_0 (stages 2-3), write y_{s+1} in FP64, i.e.
+    8/3 x 5 N x 8 bytes per cell per stage; flops: the sum-factorised volume
+    integral with the source and three owned faces."""
+    for k in (1, 2, 3):
+        N = dims(k)[0]
+        assert abs(rl.stage_min_bytes(k) - 8 / 3 * 5 * N * 8) <= 1e-9
+        assert rl.stage_flops(k, True) == rl.volume_sf_flops(k, True) + rl.face_sf_flops(k)
+    assert round(rl.stage_min_bytes(2)) == 1067
+    assert rl.stage_flops(2, True) == 13046 + 6540
+    # the fused kernel's own traffic: y_s, field, y_{s+1} every stage; d
+    # written in stages 1-2 and read in 2-3; the shadow written in stage 3
+    N, Q2, Q3 = dims(2)
+    st, f32, fld = 5 * N * 8, 5 * N * 4, 3 * Q3 * 4
+    assert abs(rl.fused_impl_bytes(2, True) - (3 * (2 * st + fld) + 4 * f32 + f32) / 3) <= 1e-9
+
+
+def test_stage_roofline_entry():
+    nc = 128 ** 3
+    e = rl.stage_roofline(2, True, nc, 2.0, 6791.7, rl.FP32_PEAK)
+    t_alu = rl.stage_flops(2, True) * nc / rl.FP32_PEAK
+    t_hbm = rl.stage_min_bytes(2) * nc / 6791.7e9
+    assert t_alu > t_hbm and e["bound"] == "alu" and e["unit"] == "TFLOP/s"
+    assert abs(e["frac"] - t_alu / 2e-3) <= 1e-12
+    assert abs(e["achieved"] / e["peak"] - e["frac"]) <= 1e-12
+    assert abs(rl.FP32_PEAK - 80.54784e12) <= 1.0
+    # FP64: the ALU time dominates too
+    f = rl.stage_roofline(2, True, nc, 50.0, 6791.7, rl.FP64_PEAK)
+    assert f["bound"] == "alu" and abs(f["frac"] - rl.stage_flops(2, True) * nc / 1.25e12 / 0.05) <= 1e-12
+
+
 def test_step_roofline_entry():
     nc = 128 ** 3
-    r = bench.step_roofline(2, True, nc, 12.4, 6780.0)
-    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
-    assert abs(r["achieved"] - 9556 * nc / 12.4e-3 / 1e9) <= 1e-9 * r["achieved"]
-    assert abs(r["frac"] - r["achieved"] / 6780.0) <= 1e-15
+    N = dims(2)[0]
+    byts = (3200 + (5 * N + 1) * 8 + 40) * nc
+    flops = 3 * rl.stage_flops(2, True) * nc
+    r = bench.step_roofline(2, True, nc, 8.0, 6780.0)
+    assert r["bytes_per_step"] == byts and r["flops_per_step"] == flops
+    assert r["bound"] == "alu" and abs(r["frac"] - flops / rl.FP32_PEAK / 8e-3) <= 1e-12
     f = bench.step_roofline(2, False, nc, 173.0, 6780.0)
-    flops = 3 * (rl.face_sf_flops(2) + rl.volume_sf_flops(2, True)) * nc
-    assert f["bound"] == "alu" and f["flops_per_step"] == flops
-    assert abs(f["frac"] - flops / 0.173 / 1.25e12) <= 1e-12
+    assert f["bound"] == "alu" and abs(f["frac"] - flops / 0.173 / 1.25e12) <= 1e-12
     assert bench.step_roofline(1, True, 512, 1.0, None)["frac"] is None

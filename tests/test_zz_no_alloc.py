@@ -21,7 +21,8 @@ def _normwise(a, b, N):
     return max(float(np.abs(a[i] - b[i]).max() / np.abs(b[i]).max()) for i in range(5))
 
 
-@pytest.mark.parametrize("order,n,prec", [(3, (12, 9, 7), 0), (4, (10, 9, 8), 0), (2, (16, 13, 11), 1)])
+@pytest.mark.parametrize("order,n,prec", [(3, (12, 9, 7), 0), (4, (10, 9, 8), 0), (2, (16, 13, 11), 1),
+                                          (3, (9, 8, 7), 1), (4, (8, 7, 6), 1), (1, (9, 8, 7), 0)])
 def test_noalloc_rhs_matches_dg_rhs_on_consecutive_calls(order, n, prec):
     import torch
     import paper_1602_09079_gb300 as dg
@@ -51,3 +52,31 @@ def test_noalloc_rejects_problems_beyond_its_scratch():
         dg.dg_rhs_noalloc(n, order, syn.GAMMA, dg.DG_PREC_FP64, y, y, 0)
     assert e.value.code == dg.DG_ERR_TOO_LARGE
     assert "32 MiB" in str(e.value)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_noalloc_nan_input_then_finite_call(prec):
+    """A non-finite input gives a non-finite R and DG_OK (no device-side
+    error reporting); the next call on a finite state is unaffected by what
+    the first one left in the shared array and matches dg_rhs again."""
+    import torch
+    import paper_1602_09079_gb300 as dg
+
+    n, order, g = (7, 6, 5), 3, syn.GAMMA
+    s = dg.Solver(n, order, g)
+    s.set_precision(prec)
+    w = syn.random_state(n, s.N, g, seed=41, high=0.01)
+    bad = w.copy()
+    bad[2, 3, 4, 4, 0] = np.nan
+    s.set_state(bad)
+    out = torch.zeros_like(s.y)
+    dg.dg_rhs_noalloc(n, order, g, prec, s.y, out, s.stream.cuda_stream)
+    torch.cuda.synchronize()
+    assert not torch.isfinite(out).all()
+    s.set_state(w)
+    ref = s.rhs(canonical=False)
+    out = torch.full_like(ref, float("nan"))
+    dg.dg_rhs_noalloc(n, order, g, prec, s.y, out, s.stream.cuda_stream)
+    torch.cuda.synchronize()
+    assert torch.isfinite(out).all()
+    assert _normwise(out.cpu().numpy(), ref.cpu().numpy(), s.N) <= (TOL64 if prec == 0 else TOLMIX)
