@@ -543,6 +543,10 @@ int fused_step(dg_ctx* c, double dt, bool force) {
     a.ctrl = c->ctrl;
     a.b0dt = (float)(b0[s] * dt);
     a.a0 = (float)a0[s];
+    a.b0dt_d = b0[s] * dt;
+    a.a0_d = a0[s];
+    a.b0_d = b0[s];
+    a.y0 = c->y;
     a.stage = s + 1;
     DG_CUDA(cudaMemsetAsync(&c->ctrl->n_flag, 0, sizeof(unsigned), c->stream));
     DG_TRY(launch(c, KC_VOLUME, [&] { return c->fz.run(force, c->flux, c->geo, a, c->stream); }));

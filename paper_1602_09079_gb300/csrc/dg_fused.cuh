@@ -10,7 +10,8 @@
 //      memory; a ring of neighbour cells around the column supplies the
 //      traces of the column's outer x and y faces;
 //  P2  one numerical flux per face point (x, y faces of the plane, and the
-//      z face between the previous plane and this one), scaled by 1/(4 dx);
+//      z face between the previous plane and this one), scaled by 1/(4 dx):
+//      the fast FP32 HLLC of the face frame, branch-free;
 //  P3  the z face between the previous plane and this one completes the
 //      previous plane's cells, then
 //  P4  finishes them: R, or the stage update y_{s+1} = y_s + delta with
@@ -40,12 +41,16 @@ struct FusedCfg {
   static constexpr int BX = 8, BY = 8, NC = BX * BY;
   static constexpr int THREADS = 5 * NC;  // one (cell, variable) per thread
   // face slots: the low face of every cell of the plane, then the high face
-  // of the last cell of every row (x) / column (y)
-  static constexpr int SX = NC + BY, SY = NC + BX, SZ = NC;
-  // shared memory, in floats: traces [5][Q2][slots] left (L) and right (R)
-  // of every face; the flux overwrites the right trace
-  static constexpr int XL = 0, XR = XL + 5 * Q2 * SX, YL = XR + 5 * Q2 * SX, YR = YL + 5 * Q2 * SY,
-                       ZR = YR + 5 * Q2 * SY, FACE_END = ZR + 5 * Q2 * SZ;
+  // of the last cell of every row (x) / column (y); z faces use the first NC
+  static constexpr int SX = NC + BY, SY = NC + BX;
+  // every direction's traces are laid out with the same slot stride SZ, so
+  // that a face point's offset is one index and the variables' offsets are
+  // compile-time constants
+  static constexpr int SZ = SX > SY ? SX : SY;
+  // shared memory, in floats: traces [5][Q2][SZ] left (L) and right (R) of
+  // every face; the flux overwrites the right trace
+  static constexpr int XL = 0, XR = XL + 5 * Q2 * SZ, YL = XR + 5 * Q2 * SZ, YR = YL + 5 * Q2 * SZ,
+                       ZR = YR + 5 * Q2 * SZ, FACE_END = ZR + 5 * Q2 * SZ;
   // volume slice (aliases the face traces, which are dead by then): values
   // [5][Q2][NC], fluxes [3*5][Q2][NC], source [4][Q2][NC]
   static constexpr int VU = 0, VF = VU + 5 * Q2 * NC, VS = VF + 15 * Q2 * NC, VOL_END = VS + 4 * Q2 * NC;
@@ -56,10 +61,10 @@ struct FusedCfg {
   // the left y traces, which are dead between the numerical fluxes and the
   // next plane's traces
   static constexpr int SMN = YL, SAB = YL + 5 * NC;
-  static_assert(10 * NC <= 5 * Q2 * SY, "screen buffers fit the left y traces");
+  static_assert(10 * NC <= 5 * Q2 * SZ, "screen buffers fit the left y traces");
   static constexpr size_t smem() { return sizeof(float) * (size_t)TOTAL; }
   static constexpr int MINB = 2;  // CTAs per SM the register budget is sized for
-  static constexpr int NFACE = (SX + SY + SZ) * Q2;
+  static constexpr int NFACE = (SX + SY + NC) * Q2;
 };
 
 // 1D tables of this translation unit's degree in the constant bank:
@@ -74,6 +79,20 @@ struct FzTab {
 };
 namespace {
 __constant__ float c_fz[FzTab<3>::SIZE];
+}
+
+// Exact zeros of the 1D tables: a Gauss rule with an odd number of points
+// has a node at 0, where the odd Legendre polynomials and the derivatives of
+// the even ones vanish, and Pt_0' = 0 everywhere. The multiply-adds by them
+// are dropped at compile time (the loops are unrolled); for finite operands
+// the sums are unchanged, bit for bit.
+template <int K>
+__host__ __device__ constexpr bool zero_p(int u, int q) {
+  return K % 2 == 0 && 2 * q == K && u % 2 == 1;
+}
+template <int K>
+__host__ __device__ constexpr bool zero_d(int u, int q) {
+  return u == 0 || (K % 2 == 0 && 2 * q == K && u % 2 == 0);
 }
 
 // mode index of the exponents along (normal, tangential 1, tangential 2) of a
@@ -127,75 +146,109 @@ __device__ __forceinline__ void prefetch_l2(const void* p) {
 #endif
 }
 
-__device__ __forceinline__ float sqrt_fast(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
+// approximate reciprocal and reciprocal square root (one MUFU operation
+// each, subnormals flushed to zero: relative error of a few ulp)
+__device__ __forceinline__ float rcp_fast(float x) {
+#ifdef __CUDA_ARCH__
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+#else
+  return 1.f / x;
+#endif
+}
+__device__ __forceinline__ float rsqrt_fast(float x) {
+#ifdef __CUDA_ARCH__
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+#else
+  return 1.f / std::sqrt(x);
+#endif
+}
+// sqrt(max(x, 0)): 0 for x <= 0, the limit of a sound speed at p -> 0+
+__device__ __forceinline__ float sqrt_fast(float x) { return x > 0.f ? x * rsqrt_fast(x) : 0.f; }
+
+// Every operation of the face flux is an explicit, separately rounded IEEE
+// operation (or an fmaf, or one MUFU approximation): the compiler may
+// neither contract nor reorder them, so a face whose flux two tiles
+// compute (column sides, segment ends) gets the same bits in both, whatever
+// the instruction schedule of each inlined copy.
+__device__ __forceinline__ float fm(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fa(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fs(float a, float b) { return __fsub_rn(a, b); }
 
 // Euler flux along x of the conserved state U (velocity v, pressure p)
 __device__ __forceinline__ void euler_flux_x(const float* U, const float* v, float p, float* F) {
   const float mn = U[1];
   F[0] = mn;
   F[1] = fmaf(mn, v[0], p);
-  F[2] = mn * v[1];
-  F[3] = mn * v[2];
-  F[4] = (U[4] + p) * v[0];
+  F[2] = fm(mn, v[1]);
+  F[3] = fm(mn, v[2]);
+  F[4] = fm(fa(U[4], p), v[0]);
 }
 
 // HLLC flux across a face with normal +x in the face's frame (Sect. 2.3),
 // the same algorithm as hllc_flux (Einfeldt wave speeds from Roe averages,
 // Toro's star states, sound speed 0 at pressures <= 0, S* = 0 for a receding
-// vacuum interface) with the FP32 path's fast reciprocal and square root
-// (MUFU reciprocal square root; relative error a few ulp, far below the
-// mixed path's FP32 quadrature error)
+// vacuum interface) with the FP32 path's fast reciprocal and square root,
+// written without branches: both sides' fluxes and the star correction of
+// the side of the contact are formed and the wave pattern selects one
+// (an operand that is not selected may be non-finite without effect)
 __device__ __forceinline__ void hllc_x_fast(const float* UL, const float* UR, float gamma, float* F) {
-  const float gm1 = gamma - 1.f;
-  const float rL = rsqrtf(UL[0]), rR = rsqrtf(UR[0]);
-  const float irL = rL * rL, irR = rR * rR;
-  const float vL[3] = {UL[1] * irL, UL[2] * irL, UL[3] * irL};
-  const float vR[3] = {UR[1] * irR, UR[2] * irR, UR[3] * irR};
-  const float pL = gm1 * (UL[4] - 0.5f * UL[0] * (vL[0] * vL[0] + vL[1] * vL[1] + vL[2] * vL[2]));
-  const float pR = gm1 * (UR[4] - 0.5f * UR[0] * (vR[0] * vR[0] + vR[1] * vR[1] + vR[2] * vR[2]));
-  const float cL = sqrt_fast(gamma * pL * irL), cR = sqrt_fast(gamma * pR * irR);
-  const float sL = UL[0] * rL, sR = UR[0] * rR;
-  const float iss = __fdividef(1.f, sL + sR);
-  float vt[3], v2 = 0.f;
+  const float gm1 = fs(gamma, 1.f);
+  const float rL = rsqrt_fast(UL[0]), rR = rsqrt_fast(UR[0]);
+  const float irL = fm(rL, rL), irR = fm(rR, rR);
+  const float vL[3] = {fm(UL[1], irL), fm(UL[2], irL), fm(UL[3], irL)};
+  const float vR[3] = {fm(UR[1], irR), fm(UR[2], irR), fm(UR[3], irR)};
+  const float kL = fmaf(vL[0], vL[0], fmaf(vL[1], vL[1], fm(vL[2], vL[2])));
+  const float kR = fmaf(vR[0], vR[0], fmaf(vR[1], vR[1], fm(vR[2], vR[2])));
+  const float pL = fm(gm1, fs(UL[4], fm(fm(0.5f, UL[0]), kL)));
+  const float pR = fm(gm1, fs(UR[4], fm(fm(0.5f, UR[0]), kR)));
+  const float cL = sqrt_fast(fm(fm(gamma, pL), irL)), cR = sqrt_fast(fm(fm(gamma, pR), irR));
+  const float sL = fm(UL[0], rL), sR = fm(UR[0], rR);
+  const float iss = rcp_fast(fa(sL, sR));
+  float vt[3];
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    vt[a] = (sL * vL[a] + sR * vR[a]) * iss;
-    v2 += vt[a] * vt[a];
-  }
-  const float Ht = (rL * (UL[4] + pL) + rR * (UR[4] + pR)) * iss;
-  const float ct = sqrt_fast(gm1 * (Ht - 0.5f * v2));
+  for (int a = 0; a < 3; ++a) vt[a] = fm(fmaf(sL, vL[a], fm(sR, vR[a])), iss);
+  const float v2 = fmaf(vt[0], vt[0], fmaf(vt[1], vt[1], fm(vt[2], vt[2])));
+  const float Ht = fm(fmaf(rL, fa(UL[4], pL), fm(rR, fa(UR[4], pR))), iss);
+  const float ct = sqrt_fast(fm(gm1, fs(Ht, fm(0.5f, v2))));
   const float uL = vL[0], uR = vR[0];
-  const float SL = fminf(uL - cL, vt[0] - ct);
-  const float SR = fmaxf(uR + cR, vt[0] + ct);
-  if (SL >= 0.f) {
-    euler_flux_x(UL, vL, pL, F);
-    return;
-  }
-  if (SR <= 0.f) {
-    euler_flux_x(UR, vR, pR, F);
-    return;
-  }
-  const float aL = UL[0] * (SL - uL), aR = UR[0] * (SR - uR);
-  const float den = aL - aR;
-  const float Ss = den == 0.f ? 0.f : __fdividef(pR - pL + uL * aL - uR * aR, den);
+  const float SL = fminf(fs(uL, cL), fs(vt[0], ct));
+  const float SR = fmaxf(fa(uR, cR), fa(vt[0], ct));
+  float FL[5], FR[5];
+  euler_flux_x(UL, vL, pL, FL);
+  euler_flux_x(UR, vR, pR, FR);
+  const float aL = fm(UL[0], fs(SL, uL)), aR = fm(UR[0], fs(SR, uR));
+  const float den = fs(aL, aR);
+  const float num = fs(fa(fs(pR, pL), fm(uL, aL)), fm(uR, aR));
+  const float Ss = den == 0.f ? 0.f : fm(num, rcp_fast(den));
   const bool left = Ss >= 0.f;
-  float U[5], v[3];
+  float U[5], FK[5];
 #pragma unroll
-  for (int i = 0; i < 5; ++i) U[i] = left ? UL[i] : UR[i];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) v[a] = left ? vL[a] : vR[a];
-  const float p = left ? pL : pR, S = left ? SL : SR, ak = left ? aL : aR, ir = left ? irL : irR, uk = v[0];
-  euler_flux_x(U, v, p, F);
-  const float isd = __fdividef(1.f, S - Ss);
-  const float chi = ak * isd;
+  for (int i = 0; i < 5; ++i) {
+    U[i] = left ? UL[i] : UR[i];
+    FK[i] = left ? FL[i] : FR[i];
+  }
+  const float v1 = left ? vL[1] : vR[1], v2t = left ? vL[2] : vR[2];
+  const float p = left ? pL : pR, S = left ? SL : SR, ak = left ? aL : aR, ir = left ? irL : irR;
+  const float uk = left ? uL : uR;
+  const float isd = rcp_fast(fs(S, Ss));
+  const float chi = fm(ak, isd);
+  const float dsu = fs(Ss, uk);
   float Us[5];
   Us[0] = chi;
-  Us[1] = chi * Ss;
-  Us[2] = chi * v[1];
-  Us[3] = chi * v[2];
-  Us[4] = chi * (U[4] * ir + (Ss - uk) * Ss) + (Ss - uk) * p * isd;
+  Us[1] = fm(chi, Ss);
+  Us[2] = fm(chi, v1);
+  Us[3] = fm(chi, v2t);
+  Us[4] = fa(fm(chi, fa(fm(U[4], ir), fm(dsu, Ss))), fm(fm(dsu, p), isd));
+  const bool supL = SL >= 0.f, supR = SR <= 0.f;
 #pragma unroll
-  for (int i = 0; i < 5; ++i) F[i] += S * (Us[i] - U[i]);
+  for (int i = 0; i < 5; ++i) {
+    const float fsi = fmaf(S, fs(Us[i], U[i]), FK[i]);
+    F[i] = supL ? FL[i] : (supR ? FR[i] : fsi);
+  }
 }
 
 // numerical flux in the face's frame: HLLC (fast FP32 form) or the exact
@@ -235,14 +288,16 @@ __device__ __forceinline__ void fz_trace(const float (&w)[nmodes(K)], float* dst
     for (int a = 0, j = 0; a <= K; ++a) {
       float s = 0.f;
 #pragma unroll
-      for (int b = 0; a + b <= K; ++b, ++j) s = fmaf(E[j], c_fz[TB::P + b * Q + t2], s);
+      for (int b = 0; a + b <= K; ++b, ++j)
+        if (!zero_p<K>(b, t2)) s = fmaf(E[j], c_fz[TB::P + b * Q + t2], s);
       H[a] = s;
     }
 #pragma unroll
     for (int t1 = 0; t1 < Q; ++t1) {
       float s = 0.f;
 #pragma unroll
-      for (int a = 0; a <= K; ++a) s = fmaf(H[a], c_fz[TB::P + a * Q + t1], s);
+      for (int a = 0; a <= K; ++a)
+        if (!zero_p<K>(a, t1)) s = fmaf(H[a], c_fz[TB::P + a * Q + t1], s);
       dst[(t1 + Q * t2) * pstride] = s;
     }
   }
@@ -265,12 +320,14 @@ __device__ __forceinline__ void fz_moments(const float* src, int pstride, float 
     for (int t1 = 0; t1 < Q; ++t1) {
       const float f = src[(t1 + Q * t2) * pstride];
 #pragma unroll
-      for (int a = 0; a <= K; ++a) G[a] = fmaf(f, c_fz[TB::PW + a * Q + t1], G[a]);
+      for (int a = 0; a <= K; ++a)
+        if (!zero_p<K>(a, t1)) G[a] = fmaf(f, c_fz[TB::PW + a * Q + t1], G[a]);
     }
 #pragma unroll
     for (int a = 0, j = 0; a <= K; ++a)
 #pragma unroll
-      for (int b = 0; a + b <= K; ++b, ++j) H[j] = fmaf(G[a], c_fz[TB::PW + b * Q + t2], H[j]);
+      for (int b = 0; a + b <= K; ++b, ++j)
+        if (!zero_p<K>(b, t2)) H[j] = fmaf(G[a], c_fz[TB::PW + b * Q + t2], H[j]);
   }
 }
 
@@ -383,6 +440,12 @@ __global__ void __launch_bounds__(FusedCfg<K>::THREADS, FusedCfg<K>::MINB) fused
   float w[N], acc[N];
 #pragma unroll
   for (int l = 0; l < N; ++l) acc[l] = 0.f;
+  // the density threads (i = 0) also sum the mean mode's face terms in FP64:
+  // each face moment is the same FP32 value in both cells that share the
+  // face, so these sums telescope and the FP64 stage update conserves mass
+  // to FP64 rounding (the FP32 sums of the other modes round independently
+  // in every cell)
+  double accm = 0.0;
 
   for (int pz = -1; pz <= vz; ++pz) {
     int zc = z0 + pz;
@@ -400,10 +463,10 @@ __global__ void __launch_bounds__(FusedCfg<K>::THREADS, FusedCfg<K>::MINB) fused
       if (cval) {
         if (pz >= 0) fz_trace<K, 2, 0>(w, sm + CF::ZR + fvz * Q2 * SZ + c, SZ);
         if (own) {
-          fz_trace<K, 0, 0>(w, sm + CF::XR + fvx * Q2 * SX + c, SX);
-          fz_trace<K, 0, 1>(w, sm + CF::XL + fvx * Q2 * SX + hx, SX);
-          fz_trace<K, 1, 0>(w, sm + CF::YR + fvy * Q2 * SY + c, SY);
-          fz_trace<K, 1, 1>(w, sm + CF::YL + fvy * Q2 * SY + hy, SY);
+          fz_trace<K, 0, 0>(w, sm + CF::XR + fvx * Q2 * SZ + c, SZ);
+          fz_trace<K, 0, 1>(w, sm + CF::XL + fvx * Q2 * SZ + hx, SZ);
+          fz_trace<K, 1, 0>(w, sm + CF::YR + fvy * Q2 * SZ + c, SZ);
+          fz_trace<K, 1, 1>(w, sm + CF::YL + fvy * Q2 * SZ + hy, SZ);
         }
       }
       // ring of neighbour cells around the column (own planes): warps 0-3
@@ -413,10 +476,10 @@ __global__ void __launch_bounds__(FusedCfg<K>::THREADS, FusedCfg<K>::MINB) fused
         const double* p = ysr + (zoff + rxy);
 #pragma unroll
         for (int l = 0; l < N; ++l, p += rs) wr[l] = f64_to_f32_q(__ldg(p));
-        if (rside == 0) fz_trace<K, 0, 1>(wr, sm + CF::XL + rfvx * Q2 * SX + rr * BX, SX);
-        else if (rside == 1) fz_trace<K, 0, 0>(wr, sm + CF::XR + rfvx * Q2 * SX + NC + rr, SX);
-        else if (rside == 2) fz_trace<K, 1, 1>(wr, sm + CF::YL + rfvy * Q2 * SY + rr, SY);
-        else fz_trace<K, 1, 0>(wr, sm + CF::YR + rfvy * Q2 * SY + NC + rr, SY);
+        if (rside == 0) fz_trace<K, 0, 1>(wr, sm + CF::XL + rfvx * Q2 * SZ + rr * BX, SZ);
+        else if (rside == 1) fz_trace<K, 0, 0>(wr, sm + CF::XR + rfvx * Q2 * SZ + NC + rr, SZ);
+        else if (rside == 2) fz_trace<K, 1, 1>(wr, sm + CF::YL + rfvy * Q2 * SZ + rr, SZ);
+        else fz_trace<K, 1, 0>(wr, sm + CF::YR + rfvy * Q2 * SZ + NC + rr, SZ);
       }
     }
     __syncthreads();
@@ -425,32 +488,49 @@ __global__ void __launch_bounds__(FusedCfg<K>::THREADS, FusedCfg<K>::MINB) fused
       const int first = own ? 0 : (SX + SY) * Q2;
 #pragma unroll 2
       for (int it = first + tid; it < CF::NFACE; it += CF::THREADS) {
-        int dir, slot, p, S, oL, oR;
+        // item -> direction, face slot and point; o = p SZ + slot is the
+        // face point's offset in its direction's trace arrays
+        int oL, oR, slot, o;
+        bool valid;
+        float sc;
         if (it < SX * Q2) {
-          dir = 0; S = SX; slot = it % SX; p = it / SX; oL = CF::XL; oR = CF::XR;
+          slot = it % SX;
+          o = (it / SX) * SZ + slot;
+          oL = CF::XL;
+          oR = CF::XR;
+          sc = scale[0];
+          valid = slot < NC ? ((slot % BX) < vx && (slot / BX) < vy) : slot - NC < vy;
         } else if (it < (SX + SY) * Q2) {
           const int r = it - SX * Q2;
-          dir = 1; S = SY; slot = r % SY; p = r / SY; oL = CF::YL; oR = CF::YR;
+          slot = r % SY;
+          o = (r / SY) * SZ + slot;
+          oL = CF::YL;
+          oR = CF::YR;
+          sc = scale[1];
+          valid = slot < NC ? ((slot % BX) < vx && (slot / BX) < vy) : slot - NC < vx;
         } else {
           const int r = it - (SX + SY) * Q2;
-          dir = 2; S = SZ; slot = r % SZ; p = r / SZ; oL = CF::ZL; oR = CF::ZR;
+          slot = r % NC;
+          o = (r / NC) * SZ + slot;
+          oL = CF::ZL;
+          oR = CF::ZR;
+          sc = scale[2];
+          valid = (slot % BX) < vx && (slot / BX) < vy;
         }
-        bool valid;
-        if (slot < NC) valid = (slot % BX) < vx && (slot / BX) < vy;
-        else valid = dir == 0 ? slot - NC < vy : slot - NC < vx;
         if (valid) {
           // both traces are stored in the face's frame (normal momentum
           // first, then the two tangential ones in ascending axis order)
+          const float* pl = sm + oL + o;
+          float* pr = sm + oR + o;
           float UL[5], UR[5], F[5];
-  #pragma unroll
+#pragma unroll
           for (int v = 0; v < 5; ++v) {
-            UL[v] = sm[oL + (v * Q2 + p) * S + slot];
-            UR[v] = sm[oR + (v * Q2 + p) * S + slot];
+            UL[v] = pl[v * Q2 * SZ];
+            UR[v] = pr[v * Q2 * SZ];
           }
           err |= face_flux_x<FLUX>(UL, UR, gam, F);
-          const float sc = dir == 0 ? scale[0] : (dir == 1 ? scale[1] : scale[2]);
-  #pragma unroll
-          for (int v = 0; v < 5; ++v) sm[oR + (v * Q2 + p) * S + slot] = F[v] * sc;
+#pragma unroll
+          for (int v = 0; v < 5; ++v) pr[v * Q2 * SZ] = F[v] * sc;
         }
       }
     }
@@ -472,11 +552,12 @@ __global__ void __launch_bounds__(FusedCfg<K>::THREADS, FusedCfg<K>::MINB) fused
               const int m = face_mode<2>(e, aa, b);
               acc[m] = fmaf(-c_fz[TB::EP + e], H[j], acc[m]);
             }
+        if (i == 0) accm -= f32_to_f64_q(H[0]);  // Pt_0(+1) = 1
         const size_t o0 = (size_t)(i * N) * rs + (size_t)(zprev + cxy);
         if (a.stage == 0) {
           double* pr = a.R + o0;
 #pragma unroll
-          for (int l = 0; l < N; ++l, pr += rs) *pr = f32_to_f64_q(-acc[l]);
+          for (int l = 0; l < N; ++l, pr += rs) *pr = (l == 0 && i == 0) ? -accm : f32_to_f64_q(-acc[l]);
         } else {
           float sab = 0.f;
           double mean = 0.0;
@@ -485,10 +566,22 @@ __global__ void __launch_bounds__(FusedCfg<K>::THREADS, FusedCfg<K>::MINB) fused
           for (int l = 0; l < N; ++l, o += rs) {
             const double ysv = __ldg(a.ys + o);
             const float dl = a.stage >= 2 ? a.d[o] : 0.f;
-            const float delta = fmaf(a.b0dt, acc[l], -a.a0 * dl);
-            const double v = ysv + f32_to_f64_q(delta);
+            double v;
+            float dnew;
+            if (l == 0 && i == 0) {
+              // mean density: the Shu-Osher combination in FP64, a0 y_0 +
+              // b0 y_s + b0 dt dw/dt, with dw/dt from the FP64 face sum (y_0
+              // is read for this one value per cell; in stage 1 y_0 = y_s)
+              const double y00 = a.stage >= 2 ? a.y0[o] : ysv;
+              v = fma(a.a0_d, y00, fma(a.b0_d, ysv, a.b0dt_d * accm));
+              dnew = f64_to_f32_q(v - y00);
+            } else {
+              const float delta = fmaf(a.b0dt, acc[l], -a.a0 * dl);
+              v = ysv + f32_to_f64_q(delta);
+              dnew = dl + delta;
+            }
             a.out[o] = v;
-            if (a.stage <= 2) a.d[o] = dl + delta;
+            if (a.stage <= 2) a.d[o] = dnew;
             else if (a.yf) a.yf[o] = f64_to_f32_q(v);
             if (l == 0) mean = v;
             else sab = fmaf(abs_up(v), c_fz[(g.lim_vol ? TB::LMV : TB::LM) + l], sab);
@@ -499,6 +592,7 @@ __global__ void __launch_bounds__(FusedCfg<K>::THREADS, FusedCfg<K>::MINB) fused
       }
 #pragma unroll
       for (int l = 0; l < N; ++l) acc[l] = 0.f;
+      if (i == 0) accm = pz >= 0 ? f32_to_f64_q(H[0]) : 0.0;  // Pt_0(-1) = 1
       if (pz >= 0) {
 #pragma unroll
         for (int aa = 0, j = 0; aa <= K; ++aa)
@@ -512,12 +606,14 @@ __global__ void __launch_bounds__(FusedCfg<K>::THREADS, FusedCfg<K>::MINB) fused
       }
       if (own) {
         float Hl[T], Hh[T];
-        fz_moments<K>(sm + CF::XR + fvx * Q2 * SX + c, SX, Hl);
-        fz_moments<K>(sm + CF::XR + fvx * Q2 * SX + hx, SX, Hh);
+        fz_moments<K>(sm + CF::XR + fvx * Q2 * SZ + c, SZ, Hl);
+        fz_moments<K>(sm + CF::XR + fvx * Q2 * SZ + hx, SZ, Hh);
         fz_apply<K, 0>(Hl, Hh, acc);
-        fz_moments<K>(sm + CF::YR + fvy * Q2 * SY + c, SY, Hl);
-        fz_moments<K>(sm + CF::YR + fvy * Q2 * SY + hy, SY, Hh);
+        if (i == 0) accm += f32_to_f64_q(Hl[0]) - f32_to_f64_q(Hh[0]);
+        fz_moments<K>(sm + CF::YR + fvy * Q2 * SZ + c, SZ, Hl);
+        fz_moments<K>(sm + CF::YR + fvy * Q2 * SZ + hy, SZ, Hh);
         fz_apply<K, 1>(Hl, Hh, acc);
+        if (i == 0) accm += f32_to_f64_q(Hl[0]) - f32_to_f64_q(Hh[0]);
       }
       // high-z traces of this plane for the next plane's z faces (the
       // previous ones were consumed in P2)
@@ -573,7 +669,8 @@ __global__ void __launch_bounds__(FusedCfg<K>::THREADS, FusedCfg<K>::MINB) fused
             for (int v = 0; u + v <= K; ++v, ++j) {
               float s = 0.f;
 #pragma unroll
-              for (int ww = 0; u + v + ww <= K; ++ww) s = fmaf(w[mode_index(u, v, ww)], c_fz[TB::P + ww * Q + qz], s);
+              for (int ww = 0; u + v + ww <= K; ++ww)
+                if (!zero_p<K>(ww, qz)) s = fmaf(w[mode_index(u, v, ww)], c_fz[TB::P + ww * Q + qz], s);
               A1[j] = s;
             }
 #pragma unroll
@@ -583,14 +680,16 @@ __global__ void __launch_bounds__(FusedCfg<K>::THREADS, FusedCfg<K>::MINB) fused
             for (int u = 0, j = 0; u <= K; ++u) {
               float s = 0.f;
 #pragma unroll
-              for (int v = 0; u + v <= K; ++v, ++j) s = fmaf(A1[j], c_fz[TB::P + v * Q + qy], s);
+              for (int v = 0; u + v <= K; ++v, ++j)
+                if (!zero_p<K>(v, qy)) s = fmaf(A1[j], c_fz[TB::P + v * Q + qy], s);
               A2[u] = s;
             }
 #pragma unroll
             for (int qx = 0; qx < Q; ++qx) {
               float s = 0.f;
 #pragma unroll
-              for (int u = 0; u <= K; ++u) s = fmaf(A2[u], c_fz[TB::P + u * Q + qx], s);
+              for (int u = 0; u <= K; ++u)
+                if (!zero_p<K>(u, qx)) s = fmaf(A2[u], c_fz[TB::P + u * Q + qx], s);
               sm[CF::VU + (i * Q2 + qx + Q * qy) * NC + c] = s;
             }
           }
@@ -622,7 +721,7 @@ __global__ void __launch_bounds__(FusedCfg<K>::THREADS, FusedCfg<K>::MINB) fused
               float U[5];
 #pragma unroll
               for (int v = 0; v < 5; ++v) U[v] = sm[CF::VU + (v * Q2 + qs) * NC + cc];
-              const float ir = __fdividef(1.f, U[0]);
+              const float ir = rcp_fast(U[0]);
               const float vel[3] = {U[1] * ir, U[2] * ir, U[3] * ir};
               const float p = gm1 * (U[4] - 0.5f * U[0] * (vel[0] * vel[0] + vel[1] * vel[1] + vel[2] * vel[2]));
 #pragma unroll
@@ -672,21 +771,25 @@ __global__ void __launch_bounds__(FusedCfg<K>::THREADS, FusedCfg<K>::MINB) fused
               const float vs_ = src ? fs[qs * NC] : 0.f;
 #pragma unroll
               for (int u = 0; u <= K; ++u) {
-                Gx[u] = fmaf(vx_, c_fz[TB::DW + u * Q + qx], Gx[u]);
-                // the source is weighted by Pt w along all three axes, like
-                // the x flux along y and z: it joins the x flux's sums here
-                if (FORCE) Gx[u] = fmaf(vs_, c_fz[TB::PW + u * Q + qx], Gx[u]);
-                Gy[u] = fmaf(vy_, c_fz[TB::PW + u * Q + qx], Gy[u]);
-                Gz[u] = fmaf(vz_, c_fz[TB::PW + u * Q + qx], Gz[u]);
+                if (!zero_d<K>(u, qx)) Gx[u] = fmaf(vx_, c_fz[TB::DW + u * Q + qx], Gx[u]);
+                if (!zero_p<K>(u, qx)) {
+                  // the source is weighted by Pt w along all three axes, like
+                  // the x flux along y and z: it joins the x flux's sums here
+                  if (FORCE) Gx[u] = fmaf(vs_, c_fz[TB::PW + u * Q + qx], Gx[u]);
+                  Gy[u] = fmaf(vy_, c_fz[TB::PW + u * Q + qx], Gy[u]);
+                  Gz[u] = fmaf(vz_, c_fz[TB::PW + u * Q + qx], Gz[u]);
+                }
               }
             }
 #pragma unroll
             for (int u = 0, j = 0; u <= K; ++u)
 #pragma unroll
               for (int v = 0; u + v <= K; ++v, ++j) {
-                H1[j] = fmaf(Gx[u], c_fz[TB::PW + v * Q + qy], H1[j]);
-                H1[j] = fmaf(Gy[u], c_fz[TB::DW + v * Q + qy], H1[j]);
-                H2[j] = fmaf(Gz[u], c_fz[TB::PW + v * Q + qy], H2[j]);
+                if (!zero_p<K>(v, qy)) {
+                  H1[j] = fmaf(Gx[u], c_fz[TB::PW + v * Q + qy], H1[j]);
+                  H2[j] = fmaf(Gz[u], c_fz[TB::PW + v * Q + qy], H2[j]);
+                }
+                if (!zero_d<K>(v, qy)) H1[j] = fmaf(Gy[u], c_fz[TB::DW + v * Q + qy], H1[j]);
               }
           }
 #pragma unroll
@@ -696,8 +799,8 @@ __global__ void __launch_bounds__(FusedCfg<K>::THREADS, FusedCfg<K>::MINB) fused
 #pragma unroll
               for (int ww = 0; u + v + ww <= K; ++ww) {
                 const int m = mode_index(u, v, ww);
-                acc[m] = fmaf(H1[j], c_fz[TB::PW + ww * Q + qz], acc[m]);
-                acc[m] = fmaf(H2[j], c_fz[TB::DW + ww * Q + qz], acc[m]);
+                if (!zero_p<K>(ww, qz)) acc[m] = fmaf(H1[j], c_fz[TB::PW + ww * Q + qz], acc[m]);
+                if (!zero_d<K>(ww, qz)) acc[m] = fmaf(H2[j], c_fz[TB::DW + ww * Q + qz], acc[m]);
               }
         }
       }

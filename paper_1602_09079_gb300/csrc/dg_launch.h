@@ -73,6 +73,8 @@ struct FusedArgs {
   int* list;           // cells failing the limiter screen
   Ctrl* ctrl;
   float b0dt, a0;      // delta = b0 dt dw/dt - a0 d
+  double b0dt_d, a0_d, b0_d;  // the same in FP64, and b0 (mean density)
+  const double* y0;    // y^(0) of the step (stages 2-3; may alias out in stage 3)
   float eps_r, eps_p;  // positivity floors (FP32) for the limiter screen
   int stage;           // 0: R(y); 1, 2, 3: SSP-RK3 stage
   int lz;              // planes per z segment

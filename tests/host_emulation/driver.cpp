@@ -247,6 +247,10 @@ static void run_step(Setup& S, std::vector<double>& y, double dt, const std::vec
       a.list = list.data();
       a.b0dt = (float)(b0[s] * dt);
       a.a0 = (float)a0[s];
+      a.b0dt_d = b0[s] * dt;
+      a.a0_d = a0[s];
+      a.b0_d = b0[s];
+      a.y0 = y.data();
       a.stage = s + 1;
       S.ctrl.n_flag = 0;
       if (force) fused_launch<true>(S, a);

@@ -211,6 +211,9 @@ struct uint4 {
 inline uint4 make_uint4(unsigned x, unsigned y, unsigned z, unsigned w) { return {x, y, z, w}; }
 inline float __expf(float x) { return std::exp(x); }
 inline float __fdividef(float a, float b) { return a / b; }
+inline float __fmul_rn(float a, float b) { return a * b; }
+inline float __fadd_rn(float a, float b) { return a + b; }
+inline float __fsub_rn(float a, float b) { return a - b; }
 // hi:lo shifted left by s mod 32, upper 32 bits
 inline unsigned __funnelshift_l(unsigned lo, unsigned hi, unsigned s) {
   return (unsigned)(((((unsigned long long)hi << 32) | lo) << (s & 31)) >> 32);
