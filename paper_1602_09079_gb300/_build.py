@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libdg_gb300.so")
-UNITS = ["dg_api.cu", "dg_k0.cu", "dg_k1.cu", "dg_k2.cu", "dg_k3.cu", "dg_f2.cu", "dg_mlp.cu", "dg_spectrum.cu"]
+UNITS = ["dg_api.cu", "dg_k0.cu", "dg_k1.cu", "dg_k2.cu", "dg_k3.cu", "dg_f2.cu", "dg_f3.cu", "dg_mlp.cu", "dg_spectrum.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -198,9 +198,10 @@ Launchers launchers_for(int k) {
   }
 }
 
-// fused FP32-mixed stage kernels exist for degree 2
+// fused FP32-mixed stage kernels exist for degrees 2 and 3
 FusedLaunchers fused_for(int k) {
   if (k == 2) return fused_launchers_k2();
+  if (k == 3) return fused_launchers_k3();
   FusedLaunchers L{};
   L.k = k;
   return L;

@@ -38,7 +38,9 @@ namespace dg {
 template <int K>
 struct FusedCfg {
   static constexpr int Q = K + 1, Q2 = Q * Q, Q3 = Q2 * Q, N = nmodes(K), T = (K + 1) * (K + 2) / 2;
-  static constexpr int BX = 8, BY = 8, NC = BX * BY;
+  // plane tile: 8 x 8 cells at degree <= 2; 8 x 4 at degree 3, whose
+  // Q^2 = 16 face points per face double the trace storage
+  static constexpr int BX = 8, BY = K >= 3 ? 4 : 8, NC = BX * BY;
   static constexpr int THREADS = 5 * NC;  // one (cell, variable) per thread
   // face slots: the low face of every cell of the plane, then the high face
   // of the last cell of every row (x) / column (y); z faces use the first NC
@@ -63,7 +65,7 @@ struct FusedCfg {
   static constexpr int SMN = YL, SAB = YL + 5 * NC;
   static_assert(10 * NC <= 5 * Q2 * SZ, "screen buffers fit the left y traces");
   static constexpr size_t smem() { return sizeof(float) * (size_t)TOTAL; }
-  static constexpr int MINB = 2;  // CTAs per SM the register budget is sized for
+  static constexpr int MINB = K >= 3 ? 3 : 2;  // CTAs per SM the register budget is sized for
   static constexpr int NFACE = (SX + SY + NC) * Q2;
 };
 
@@ -415,13 +417,32 @@ __global__ void __launch_bounds__(FusedCfg<K>::THREADS, FusedCfg<K>::MINB) fused
   const int cxy = cval ? gy * g.nx + gx : y0 * g.nx + x0;  // in-plane index of this thread's cell
   const size_t rs = (size_t)nc;                            // row stride of the state layout
   const double* ysi = a.ys + (size_t)(i * N) * rs;         // this thread's variable
-  // ring item of threads 0..159 (own planes): warps 0-3 take one side each
-  // for variables 0-3, warp 4 variable 4 of all sides
-  const int rwv = tid >> 5, rlane = tid & 31;
-  const int rside = rwv < 4 ? rwv : rlane >> 3;
-  const int riv = rwv < 4 ? rlane >> 3 : 4;
-  const int rr = rlane & 7;  // row (x sides) or column (y sides)
-  const bool rval = tid < 5 * 32 && (rside < 2 ? rr < vy : rr < vx);
+  // ring items (own planes): one (side, variable, row or column) per thread.
+  // 8 x 8 tiles: warps 0-3 take one side each for variables 0-3, warp 4
+  // variable 4 of all sides (no divergence between trace variants within
+  // warps 0-3); other tiles: side-major order
+  int rside, riv, rr;
+  if constexpr (BX == 8 && BY == 8) {
+    const int rwv = tid >> 5, rlane = tid & 31;
+    rside = rwv < 4 ? rwv : rlane >> 3;
+    riv = rwv < 4 ? rlane >> 3 : 4;
+    rr = rlane & 7;  // row (x sides) or column (y sides)
+  } else {
+    int t = tid;
+    if (t < 10 * BY) {
+      rside = t / (5 * BY);
+      t -= rside * 5 * BY;
+      riv = t / BY;
+      rr = t - riv * BY;
+    } else {
+      t -= 10 * BY;
+      rside = 2 + t / (5 * BX);
+      t -= (rside - 2) * 5 * BX;
+      riv = t / BX;
+      rr = t - riv * BX;
+    }
+  }
+  const bool rval = tid < 10 * (BX + BY) && (rside < 2 ? rr < vy : rr < vx);
   int rxy = 0;
   {
     int rx, ry;
@@ -431,7 +452,7 @@ __global__ void __launch_bounds__(FusedCfg<K>::THREADS, FusedCfg<K>::MINB) fused
     else { rx = x0 + rr; ry = y0 + vy >= g.ny ? y0 + vy - g.ny : y0 + vy; }
     if (rval) rxy = ry * g.nx + rx;
   }
-  const double* ysr = a.ys + (size_t)(riv * N) * rs;
+  const double* ysr = a.ys + (size_t)((rval ? riv : 0) * N) * rs;
   // this thread's variable (and its ring item's) in each face frame
   const int fvx = face_var(0, i), fvy = face_var(1, i), fvz = face_var(2, i);
   const int rfvx = face_var(0, riv), rfvy = face_var(1, riv);

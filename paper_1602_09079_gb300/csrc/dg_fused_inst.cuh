@@ -4,6 +4,8 @@
 #include "dg_fused.cuh"
 #include "dg_launch.h"
 
+#include <algorithm>
+
 #ifndef DG_K
 #error "define DG_K before including dg_fused_inst.cuh"
 #endif

@@ -91,6 +91,7 @@ struct FusedLaunchers {
 };
 
 FusedLaunchers fused_launchers_k2();
+FusedLaunchers fused_launchers_k3();
 
 Launchers launchers_k0();
 Launchers launchers_k1();

@@ -22,7 +22,7 @@
 //       the FP32 and FP64 HLLC (or exact-Riemann) fluxes of one face point
 //
 // prec: 0 FP64, 1 mixed; flux: 0 HLLC (default), 1 exact Riemann solver.
-// Degree 2 in mixed precision runs the fused stage kernel (dg_fused.cuh) as
+// Degrees 2 and 3 in mixed precision run the fused stage kernel (dg_fused.cuh) as
 // the library does; DG_EMU_FUSED=0 in the environment selects the separate
 // face and volume kernels instead.
 // States in the state layout [5][N][n_cells], FP64.
@@ -30,7 +30,7 @@
 #include <type_traits>
 
 #include "dg_kernels.cuh"
-#if DG_K == 2
+#if DG_K >= 2
 #include "dg_fused.cuh"
 #endif
 using namespace dg;
@@ -93,7 +93,7 @@ static void make_setup(Setup& S, int nx, int ny, int nz, double gamma, int lim_v
 static int g_flux = 0;
 
 static bool use_fused() {
-#if DG_K == 2
+#if DG_K >= 2
   const char* e = std::getenv("DG_EMU_FUSED");
   return !(e && e[0] == '0');
 #else
@@ -101,7 +101,7 @@ static bool use_fused() {
 #endif
 }
 
-#if DG_K == 2
+#if DG_K >= 2
 // the fused kernel's 1D tables (as its upload builds them) and one launch
 // with the launcher's grid and planes per segment
 static void fused_setup(const Setup& S) {
@@ -184,7 +184,7 @@ static void volume(Setup& S, const double* ys, float* yf, const T* fh, const T* 
 
 template <typename T>
 static void run_rhs(Setup& S, std::vector<double>& y, std::vector<double>& R) {
-#if DG_K == 2
+#if DG_K >= 2
   if (sizeof(T) == 4 && use_fused()) {
     fused_setup(S);
     FusedArgs a{};
@@ -229,7 +229,7 @@ static void run_step(Setup& S, std::vector<double>& y, double dt, const std::vec
   std::vector<int> list(nc, -1);
   const double a0[3] = {0.0, 0.75, 1.0 / 3.0}, b0[3] = {1.0, 0.25, 2.0 / 3.0};
   const double* ys = y.data();
-#if DG_K == 2
+#if DG_K >= 2
   if (shadow && use_fused()) {
     // the C ABI's fused step: y -> ybuf -> ybuf2 -> y with the FP32
     // increment of the step; the limiter recomputes it for changed cells
