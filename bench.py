@@ -64,6 +64,13 @@ def parse():
                     help="convergence sweep of the smooth diagonal density wave (16^3..64^3, orders 2..4, t = 1)")
     ap.add_argument("--sweep-max-cells", type=int, default=64 ** 3 * 10 // 4,
                     help="skip (n, order) pairs with n^3 N(k) above this many DOF per variable x 4")
+    ap.add_argument("--indicator", action="store_true",
+                    help="learned troubled-cell indicator at size: train on the GPU (32^3 label runs), then "
+                         "recall, misses and gated vs ungated step time on held-out 128^3 supersonic "
+                         "turbulence and a Sod tube (config 5)")
+    ap.add_argument("--ind-train-n", type=int, default=32)
+    ap.add_argument("--ind-train-steps", type=int, default=800)
+    ap.add_argument("--ind-timed-steps", type=int, default=10)
     ap.add_argument("--precisions", default="fp64,mixed",
                     help="comma list of fp64,mixed (the first listed of mixed/fp64 is the headline)")
     return ap.parse_args()
@@ -524,6 +531,181 @@ def run_reference(args):
     }))
 
 
+# ------------------------------------------------- learned indicator (config 5)
+def _ind_snapshots(dgm, torch, fn, n, steps, every, courant=0.15, precision=0):
+    """Runs of the solver with the plain limiter from the state fn; every
+    `every` steps the features and plain-indicator labels of the cells that
+    fail the limiter's screen (dg_indicator_capture)."""
+    order = 3
+    nf, F, npar, work = dgm.dg_indicator_sizes(order)
+    s = dgm.Solver((n, n, n), order, GAMMA)
+    s.set_precision(precision)
+    s.project_fn(fn)
+    X = torch.empty((s.ncells, F), dtype=torch.bfloat16, device="cuda")
+    fl = torch.empty(s.ncells, dtype=torch.int8, device="cuda")
+    sc = torch.empty(s.ncells, dtype=torch.uint8, device="cuda")
+    xs, ys = [], []
+    for it in range(steps):
+        dt = s.cfl_dt(courant)
+        s.step(dt)
+        if it % every == every - 1:
+            dgm.dg_indicator_capture(s.ctx, dt, X, fl, sc)
+            m = sc.bool()
+            if int(((fl != 0) & ~m).sum()) != 0:
+                raise RuntimeError("the limiter screen missed a troubled cell")
+            xs.append(X[m].clone())
+            ys.append((fl[m] != 0).float())
+    s.check()
+    del s, X, fl, sc
+    torch.cuda.empty_cache()
+    return torch.cat(xs), torch.cat(ys)
+
+
+def _ind_init(F, seed):
+    """He-uniform weights, zero biases; flat layout [W1 b1 W2 b2 w3 b3]."""
+    H = 64
+    rng = np.random.default_rng(seed)
+    lim1, lim2 = math.sqrt(6.0 / F), math.sqrt(6.0 / H)
+    parts = [rng.uniform(-lim1, lim1, H * F), np.zeros(H), rng.uniform(-lim2, lim2, H * H), np.zeros(H),
+             rng.uniform(-lim2, lim2, H), np.zeros(1)]
+    return np.concatenate(parts).astype(np.float32)
+
+
+def run_indicator(args):
+    """Config 5: the BF16 troubled-cell network trained on the GPU by the
+    library's backward and Adam kernels from plain-indicator labels of 32^3
+    supersonic-turbulence and Sod-tube runs (FP64 path), its threshold set so
+    that 99% of the validation runs' troubled cells pass; then at 128^3, on
+    held-out supersonic turbulence (rms Mach 2.5) and a held-out Sod tube:
+    recall and misses judged by the plain indicator, and the mixed-path step
+    time (CUDA events on the solver's stream, the gate's features and network
+    included) with the network gating the full limiter vs without it."""
+    import torch
+    import paper_1602_09079_gb300 as dgm
+    dgm.load()
+    order, n_tr, n = 3, args.ind_train_n, args.n
+    nf, F, npar, work = dgm.dg_indicator_sizes(order)
+    t0 = time.perf_counter()
+
+    def data(specs, nn):
+        xs, ys = [], []
+        for kind, seed, mach in specs:
+            if kind == "super":
+                x, y = _ind_snapshots(dgm, torch, syn.supersonic_velocity(seed, mach, GAMMA), nn, 240, 30)
+            else:
+                x, y = _ind_snapshots(dgm, torch, syn.sod_tube(seed, GAMMA)[0], nn, 120, 20)
+            xs.append(x)
+            ys.append(y)
+        return torch.cat(xs), torch.cat(ys)
+
+    Xtr, ytr = data([("super", 1, 2.0), ("super", 2, 2.5), ("super", 3, 3.0), ("super", 4, 2.5),
+                     ("sod", 1, 0), ("sod", 2, 0)], n_tr)
+    Xva, yva = data([("super", 9, 2.5), ("sod", 6, 0)], n_tr)
+    P = torch.from_numpy(_ind_init(F, 70)).cuda()
+    m1, m2 = torch.zeros_like(P), torch.zeros_like(P)
+    G = torch.zeros(npar + 1, dtype=torch.float32, device="cuda")
+    Wk = torch.empty(work, dtype=torch.uint8, device="cuda")
+    pos = float(ytr.sum())
+    pw = max(1.0, (len(ytr) - pos) / max(pos, 1.0))
+    losses = []
+    torch.cuda.synchronize()
+    tt = time.perf_counter()
+    for step in range(1, args.ind_train_steps + 1):
+        dgm.dg_indicator_backward(order, Xtr, ytr, len(ytr), pw, P, G, Wk, work, 0)
+        if step in (1, args.ind_train_steps):
+            losses.append(float(G[npar]))
+        dgm.dg_indicator_adam(P, m1, m2, G, npar, 3e-3, 0.9, 0.999, 1e-8, step, 0)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - tt
+
+    def prob(X):
+        out = torch.empty(len(X), dtype=torch.float32, device="cuda")
+        dgm.dg_indicator_forward(order, X, len(X), P, out, 0)
+        return torch.sigmoid(out)
+
+    thr = float(torch.quantile(prob(Xva)[yva > 0].float(), 0.01))
+    thr = max(min(thr, 0.999), 1e-12)
+    rows_tr = len(ytr)
+    del Xtr, ytr, Xva, yva
+    torch.cuda.empty_cache()
+
+    out = {"metric": "learned troubled-cell indicator at 128^3, order 3 (config 5)", "n": n, "order": order,
+           "train": {"n": n_tr, "rows": rows_tr, "adam_steps": args.ind_train_steps, "loss_first_last": losses,
+                     "seconds": train_s, "pos_weight": pw},
+           "threshold": thr, "workloads": {}}
+    for kind, seed, mach in (("supersonic turbulence, rms Mach 2.5 (seed 7)", 7, 2.5),
+                             ("Sod tube (seed 5)", 5, 0.0)):
+        fn = syn.supersonic_velocity(seed, mach, GAMMA) if mach > 0 else syn.sod_tube(seed, GAMMA)[0]
+        # held-out recall and misses at 128^3: FP64 runs, captures every 20 steps
+        Xte, yte = _ind_snapshots(dgm, torch, fn, n, 60, 20)
+        pte = prob(Xte)
+        sel = pte >= thr
+        tro = yte > 0
+        rec = {"captured_rows": len(yte), "troubled": int(tro.sum()),
+               "recall": float((sel & tro).sum()) / max(float(tro.sum()), 1.0),
+               "misses": int((~sel & tro).sum()), "false_flags": int((sel & ~tro).sum()),
+               "evaluated_fraction": float(sel.float().mean())}
+        del Xte, yte, pte, sel, tro
+        torch.cuda.empty_cache()
+        # timing at 128^3 on the mixed path from the same evolved state
+        s = dgm.Solver((n, n, n), order, GAMMA)
+        s.set_precision(dgm.DG_PREC_MIXED)
+        s.project_fn(fn)
+        for _ in range(20):
+            s.step(s.cfl_dt(0.15))
+        s.check()
+        w = s.get_state()
+        dt = s.cfl_dt(0.15)
+        timing = {}
+        for gate in (False, True):
+            s2 = dgm.Solver((n, n, n), order, GAMMA)
+            s2.set_precision(dgm.DG_PREC_MIXED)
+            s2.set_state(w)
+            if gate:
+                dgm.dg_set_indicator(s2.ctx, P, thr)
+            for _ in range(args.warmup):
+                s2.step(dt)
+            s2.set_state(w)
+            s2.limit()  # the step's input limited before the timed region, as after any step
+            dgm.dg_limiter_counts(s2.ctx)  # reads and clears the totals
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(s2.stream)
+            for _ in range(args.ind_timed_steps):
+                s2.step(dt)
+            e1.record(s2.stream)
+            torch.cuda.synchronize()
+            ok = True
+            try:
+                s2.check()
+            except dgm.DGError:
+                ok = False
+            q1 = dgm.dg_limiter_counts(s2.ctx)
+            s2.set_timing(True)
+            s2.set_state(w)
+            s2.limit()
+            s2.kernel_stats()
+            for _ in range(2):
+                s2.step(dt)
+            kst = s2.kernel_stats()
+            s2.set_timing(False)
+            timing["gated" if gate else "ungated"] = {
+                "ms_per_step": e0.elapsed_time(e1) / args.ind_timed_steps,
+                "screen_failures_per_step": q1[0] / args.ind_timed_steps,
+                "full_limiter_cells_per_step": q1[1] / args.ind_timed_steps,
+                "limiter_ms_per_step": kst["limiter"][1] / 2, "stage_ms_per_step": kst["volume"][1] / 2,
+                "positivity_ok": ok}
+            del s2
+            torch.cuda.empty_cache()
+        timing["speedup_gated"] = timing["ungated"]["ms_per_step"] / timing["gated"]["ms_per_step"]
+        out["workloads"][kind] = {"heldout_fp64_captures": rec, "mixed_step_timing": timing, "dt": dt}
+        del s
+        torch.cuda.empty_cache()
+    out["seconds"] = time.perf_counter() - t0
+    print(json.dumps(out))
+
+
 def l2_density_error(w, k, n, exact, nq=6):
     """L2 error of the density polynomial against exact(x, y, z) with an
     nq-point Gauss rule per axis per cell (numpy Legendre basis)."""
@@ -588,6 +770,9 @@ def main():
         args.err_steps = 200 if args.order <= 3 else 100
     if args.sweep:
         run_sweep(args)
+        return
+    if args.indicator:
+        run_indicator(args)
         return
     if args.impl == "reference":
         run_reference(args)
