@@ -1430,6 +1430,16 @@ __global__ void __launch_bounds__(kThreads) cfl_kernel(const double* __restrict_
 // (e_before - e_after), e = E - |m|^2 / (2 rho) from the means.
 // Constants of the energy reset in the kernel's arithmetic type, prepared
 // on the host (the FP32 kernel then does no per-thread FP64 set-up work).
+// a table entry of the energy reset: the FP32 path reads the constant bank
+// (its indices are warp-uniform: one broadcast per warp), the FP64 path its
+// device table through the read-only cache
+template <typename T>
+__device__ __forceinline__ T reset_tab(const T* tab, int i);
+template <>
+__device__ __forceinline__ float reset_tab<float>(const float*, int i) { return c_tab32[i]; }
+template <>
+__device__ __forceinline__ double reset_tab<double>(const double* tab, int i) { return __ldg(tab + i); }
+
 template <typename T>
 struct ResetConsts {
   T c2g, inv_rho0, gm1;  // c^2/(gamma-1), 1/rho0, gamma-1
@@ -1481,13 +1491,12 @@ __global__ void __launch_bounds__(kThreads) energy_reset_kernel(double* __restri
   const T tc2g = rc.c2g, tir0 = rc.inv_rho0;
   for (int it = tid; it < Q3 * C; it += kThreads) {
     const int c = it % C, q = it / C;
-    const T* ph = tab + TB::VPHI + q * N;
     T U[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       T a = T(0);
 #pragma unroll
-      for (int l = 0; l < N; ++l) a += sW[(i * N + l) * C + c] * __ldg(ph + l);
+      for (int l = 0; l < N; ++l) a += sW[(i * N + l) * C + c] * reset_tab<T>(tab, TB::VPHI + q * N + l);
       U[i] = a;
     }
     // gamma = 5/3 (gamma - 1 within 1e-15 of 2/3): x^(2/3) as cbrt(x)^2
@@ -1506,7 +1515,8 @@ __global__ void __launch_bounds__(kThreads) energy_reset_kernel(double* __restri
   for (int it = tid; it < N * C; it += kThreads) {
     const int c = it % C, l = it / C;
     T acc = T(0);
-    for (int q = 0; q < Q3; ++q) acc += sE[q * C + c] * __ldg(tab + TB::VPHIW + q * N + l);
+#pragma unroll 9
+    for (int q = 0; q < Q3; ++q) acc += sE[q * C + c] * reset_tab<T>(tab, TB::VPHIW + q * N + l);
     if constexpr (sizeof(T) == 4) sEn[l * C + c] = f32_to_f64(acc);
     else sEn[l * C + c] = acc;
   }
