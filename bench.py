@@ -69,7 +69,7 @@ def parse():
                          "recall, misses and gated vs ungated step time on held-out 128^3 supersonic "
                          "turbulence and a Sod tube (config 5)")
     ap.add_argument("--ind-train-n", type=int, default=32)
-    ap.add_argument("--ind-train-steps", type=int, default=800)
+    ap.add_argument("--ind-train-steps", type=int, default=3000)
     ap.add_argument("--ind-timed-steps", type=int, default=10)
     ap.add_argument("--precisions", default="fp64,mixed",
                     help="comma list of fp64,mixed (the first listed of mixed/fp64 is the headline)")
@@ -642,7 +642,7 @@ def run_indicator(args):
         sel = pte >= thr
         tro = yte > 0
         rec = {"captured_rows": len(yte), "troubled": int(tro.sum()),
-               "recall": float((sel & tro).sum()) / max(float(tro.sum()), 1.0),
+               "recall": (float((sel & tro).sum()) / float(tro.sum())) if int(tro.sum()) > 0 else None,
                "misses": int((~sel & tro).sum()), "false_flags": int((sel & ~tro).sum()),
                "evaluated_fraction": float(sel.float().mean())}
         del Xte, yte, pte, sel, tro

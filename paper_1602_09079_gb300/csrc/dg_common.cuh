@@ -457,14 +457,73 @@ __device__ __forceinline__ double positivity_tau(const double* qb, const double*
   return tau;
 }
 
+// Second sufficient test of the positivity limiter, for cells whose modal
+// bound fails: density and pressure at every point of the limiter's point
+// set (S, and the volume Gauss points when vol), evaluated in FP32 from the
+// coefficients rounded to FP32 (tab32: the FP32 copy of the degree's table).
+// A point value u = sum_l w_l phi_l computed so carries an error of at most
+// (N + 3) 2^-24 sum_l |w_l phi_l| <= 2e-6 (|w_0| + sabs_u) for N <= 20
+// (rounding of the coefficients, of the table entries and of the N products
+// and sums), so e_u = 2e-6 (|mean_u| + sabs_u) bounds it; with these bounds
+// the density and the pressure (bounded below through the density's lower
+// and the momenta's upper bounds, multiplied through by the density bound)
+// must clear the floors with a further 1e-5 relative margin, which covers
+// the FP32 rounding of the test itself. True when the cell provably needs
+// no limiting (theta1 = theta2 = 1): the FP64 limiter would leave it as it is.
+template <int K>
+__device__ bool point_screen_f32(const double* w, long long stride, const float* __restrict__ tab32,
+                                 const double* mean, const double* sabs, double gamma, double eps_r, double eps_p,
+                                 int vol) {
+  using TB = Tab<K>;
+  constexpr int N = TB::N;
+  float wf[5 * N];
+#pragma unroll
+  for (int j = 0; j < 5 * N; ++j) wf[j] = f64_to_f32(w[j * stride]);
+  float e[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) e[i] = f64_to_f32(2e-6 * (fabs(mean[i]) + sabs[i]));
+  const float thr_r = f64_to_f32(eps_r * (1.0 + 1e-6) + 1e-5 * (fabs(mean[0]) + sabs[0]));
+  const float eps_pf = f64_to_f32(eps_p * (1.0 + 1e-6));
+  const float gm1 = f64_to_f32(gamma - 1.0);
+  const int npts = TB::NL + (vol ? TB::Q3 : 0);
+  for (int s = 0; s < npts; ++s) {
+    const float* ph = s < TB::NL ? tab32 + TB::LPHI + s * N : tab32 + TB::VPHI + (s - TB::NL) * N;
+    float U[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      float a = 0.f;
+#pragma unroll
+      for (int l = 0; l < N; ++l) a = fmaf(wf[i * N + l], __ldg(ph + l), a);
+      U[i] = a;
+    }
+    const float rlo = U[0] - e[0];
+    if (!(rlo >= thr_r)) return false;
+    float k2 = 0.f;
+#pragma unroll
+    for (int a = 1; a <= 3; ++a) {
+      const float mh = fabsf(U[a]) + e[a];
+      k2 = fmaf(mh, mh, k2);
+    }
+    k2 *= 0.5f;
+    const float elo = U[4] - e[4];
+    const float lhs = gm1 * fmaf(elo, rlo, -k2);
+    const float rhs = fmaf(eps_pf, rlo, 1e-5f * gm1 * fmaf(fabsf(U[4]) + e[4], rlo, k2));
+    if (!(lhs >= rhs)) return false;
+  }
+  return true;
+}
+
 // Zhang-Shu positivity limiter of one cell (Sect. 2.5) on its 5N FP64
 // coefficients w[(i*N + l) * stride]. A cheap sufficient test (mean minus
 // the sum of |w_l| max_S |phi_l|, with a rounding margin) skips the point
-// evaluations when the limiter provably leaves the cell unchanged.
+// evaluations when the limiter provably leaves the cell unchanged; with an
+// FP32 table (tab32 != nullptr) the FP32 point screen (point_screen_f32)
+// follows before the FP64 point evaluations.
 // Returns flag bits (1: theta1 < 1, 2: theta2 < 1) and ORs errors into err.
 template <int K>
 __device__ int limit_cell(double* w, long long stride, const double* __restrict__ tab, double gamma,
-                          double eps_r, double eps_p, unsigned* err, int vol) {
+                          double eps_r, double eps_p, unsigned* err, int vol,
+                          const float* __restrict__ tab32 = nullptr) {
   using TB = Tab<K>;
   constexpr int N = TB::N;
   const double gm1 = gamma - 1.0;
@@ -499,6 +558,24 @@ __device__ int limit_cell(double* w, long long stride, const double* __restrict_
   // density: theta1
   double rlo = mean[0] - sabs[0];
   bool rho_safe = rlo >= eps_r + 1e-13 * (fabs(mean[0]) + sabs[0]);
+  if (tab32) {
+    // the modal pressure bound (as below); when both modal bounds hold the
+    // point evaluations below are skipped anyway
+    bool p_modal = false;
+    if (rho_safe) {
+      const double elo = mean[4] - sabs[4];
+      double kin = 0.0;
+#pragma unroll
+      for (int a = 1; a <= 3; ++a) {
+        const double mh = fabs(mean[a]) + sabs[a];
+        kin += mh * mh;
+      }
+      kin *= 0.5 / rlo;
+      p_modal = gm1 * (elo - kin) >= eps_p + 1e-13 * gm1 * (fabs(mean[4]) + sabs[4] + kin);
+    }
+    if (!(rho_safe && p_modal) && point_screen_f32<K>(w, stride, tab32, mean, sabs, gamma, eps_r, eps_p, vol))
+      return 0;
+  }
   if (!rho_safe) {
     double rmin = mean[0];
     for (int s = 0; s < npts; ++s) {

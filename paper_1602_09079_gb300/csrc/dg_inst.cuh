@@ -201,7 +201,8 @@ cudaError_t volume_stage(int prec, bool force, const void* fh, const void* field
 
 cudaError_t limit_list(double* y, const int* list, const unsigned* count, const Geo& g, Ctrl* ctrl, int count_queued,
                        float* yf, const double* y0, float* d, cudaStream_t s) {
-  limit_list_kernel<KK><<<152, kThreads, 0, s>>>(y, list, count, tab_ptr<double>(), g, ctrl, count_queued, yf, y0, d);
+  limit_list_kernel<KK><<<152, kThreads, 0, s>>>(y, list, count, tab_ptr<double>(), g, ctrl, count_queued, yf, y0, d,
+                                                  tab_ptr<float>());
   return cudaGetLastError();
 }
 
@@ -211,7 +212,7 @@ cudaError_t screen(const double* y, uint8_t* scr, const Geo& g, cudaStream_t s) 
 }
 
 cudaError_t limit(double* y, int8_t* flags, const Geo& g, Ctrl* ctrl, cudaStream_t s) {
-  limit_kernel<KK><<<grid1(g.nc, kThreads), kThreads, 0, s>>>(y, flags, tab_ptr<double>(), g, ctrl);
+  limit_kernel<KK><<<grid1(g.nc, kThreads), kThreads, 0, s>>>(y, flags, tab_ptr<double>(), g, ctrl, tab_ptr<float>());
   return cudaGetLastError();
 }
 

@@ -701,7 +701,7 @@ __global__ void __launch_bounds__(kThreads) limit_list_kernel(double* __restrict
                                                               const unsigned* count, const double* __restrict__ tab64,
                                                               Geo g, Ctrl* ctrl, int count_queued,
                                                               float* __restrict__ yf, const double* __restrict__ y0,
-                                                              float* __restrict__ dinc) {
+                                                              float* __restrict__ dinc, const float* __restrict__ tab32) {
   constexpr int N = nmodes(K);
   const unsigned n = *count;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -711,7 +711,7 @@ __global__ void __launch_bounds__(kThreads) limit_list_kernel(double* __restrict
   unsigned e = 0;
   for (unsigned i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) {
     const long long cell = list[i];
-    if (limit_cell<K>(y + cell, g.nc, tab64, g.gamma, g.eps_rho, g.eps_p, &e, g.lim_vol)) {
+    if (limit_cell<K>(y + cell, g.nc, tab64, g.gamma, g.eps_rho, g.eps_p, &e, g.lim_vol, tab32)) {
       if (yf)
         for (int r = 0; r < 5 * N; ++r) yf[(size_t)r * g.nc + cell] = (float)y[(size_t)r * g.nc + cell];
       if (dinc)
@@ -1352,7 +1352,8 @@ __global__ void __launch_bounds__(kThreads) volume_sfb_kernel(const double* __re
 // ------------------------------------------------------ standalone limiter
 template <int K>
 __global__ void __launch_bounds__(kThreads) limit_kernel(double* __restrict__ y, int8_t* __restrict__ flags,
-                                                         const double* __restrict__ tab64, Geo g, Ctrl* ctrl) {
+                                                         const double* __restrict__ tab64, Geo g, Ctrl* ctrl,
+                                                         const float* __restrict__ tab32) {
   __shared__ unsigned s_err;
   __shared__ unsigned s_cnt;
   if (threadIdx.x == 0) {
@@ -1363,7 +1364,7 @@ __global__ void __launch_bounds__(kThreads) limit_kernel(double* __restrict__ y,
   const long long cell = (long long)blockIdx.x * kThreads + threadIdx.x;
   if (cell < g.nc) {
     unsigned e = 0;
-    int f = limit_cell<K>(y + cell, g.nc, tab64, g.gamma, g.eps_rho, g.eps_p, &e, g.lim_vol);
+    int f = limit_cell<K>(y + cell, g.nc, tab64, g.gamma, g.eps_rho, g.eps_p, &e, g.lim_vol, tab32);
     if (flags) flags[cell] = (int8_t)f;
     if (f) atomicAdd(&s_cnt, 1u);
     if (e) atomicOr(&s_err, e);
@@ -1430,16 +1431,6 @@ __global__ void __launch_bounds__(kThreads) cfl_kernel(const double* __restrict_
 // (e_before - e_after), e = E - |m|^2 / (2 rho) from the means.
 // Constants of the energy reset in the kernel's arithmetic type, prepared
 // on the host (the FP32 kernel then does no per-thread FP64 set-up work).
-// a table entry of the energy reset: the FP32 path reads the constant bank
-// (its indices are warp-uniform: one broadcast per warp), the FP64 path its
-// device table through the read-only cache
-template <typename T>
-__device__ __forceinline__ T reset_tab(const T* tab, int i);
-template <>
-__device__ __forceinline__ float reset_tab<float>(const float*, int i) { return c_tab32[i]; }
-template <>
-__device__ __forceinline__ double reset_tab<double>(const double* tab, int i) { return __ldg(tab + i); }
-
 template <typename T>
 struct ResetConsts {
   T c2g, inv_rho0, gm1;  // c^2/(gamma-1), 1/rho0, gamma-1
@@ -1491,12 +1482,13 @@ __global__ void __launch_bounds__(kThreads) energy_reset_kernel(double* __restri
   const T tc2g = rc.c2g, tir0 = rc.inv_rho0;
   for (int it = tid; it < Q3 * C; it += kThreads) {
     const int c = it % C, q = it / C;
+    const T* ph = tab + TB::VPHI + q * N;
     T U[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       T a = T(0);
 #pragma unroll
-      for (int l = 0; l < N; ++l) a += sW[(i * N + l) * C + c] * reset_tab<T>(tab, TB::VPHI + q * N + l);
+      for (int l = 0; l < N; ++l) a += sW[(i * N + l) * C + c] * __ldg(ph + l);
       U[i] = a;
     }
     // gamma = 5/3 (gamma - 1 within 1e-15 of 2/3): x^(2/3) as cbrt(x)^2
@@ -1515,8 +1507,7 @@ __global__ void __launch_bounds__(kThreads) energy_reset_kernel(double* __restri
   for (int it = tid; it < N * C; it += kThreads) {
     const int c = it % C, l = it / C;
     T acc = T(0);
-#pragma unroll 9
-    for (int q = 0; q < Q3; ++q) acc += sE[q * C + c] * reset_tab<T>(tab, TB::VPHIW + q * N + l);
+    for (int q = 0; q < Q3; ++q) acc += sE[q * C + c] * __ldg(tab + TB::VPHIW + q * N + l);
     if constexpr (sizeof(T) == 4) sEn[l * C + c] = f32_to_f64(acc);
     else sEn[l * C + c] = acc;
   }

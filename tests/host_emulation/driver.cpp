@@ -218,7 +218,7 @@ static void run_step(Setup& S, std::vector<double>& y, double dt, const std::vec
     });
   const T* fld = force ? field.data() : nullptr;
   emu::launch(grid1(nc, kThreads), kThreads, 0,
-              [&] { limit_kernel<K>(y.data(), nullptr, S.t64.data(), S.g, &S.ctrl); });
+              [&] { limit_kernel<K>(y.data(), nullptr, S.t64.data(), S.g, &S.ctrl, S.t32.data()); });
   const bool shadow = sizeof(T) == 4;
   std::vector<float> yf(shadow ? y.size() : 1);
   if (shadow)
@@ -257,7 +257,7 @@ static void run_step(Setup& S, std::vector<double>& y, double dt, const std::vec
       else fused_launch<false>(S, a);
       emu::launch(152, kThreads, 0, [&] {
         limit_list_kernel<K>(out, list.data(), &S.ctrl.n_flag, S.t64.data(), S.g, &S.ctrl, 1, s == 2 ? yfp : nullptr,
-                             s < 2 ? y.data() : nullptr, s < 2 ? dinc.data() : nullptr);
+                             s < 2 ? y.data() : nullptr, s < 2 ? dinc.data() : nullptr, S.t32.data());
       });
       ys = out;
     }
@@ -271,7 +271,8 @@ static void run_step(Setup& S, std::vector<double>& y, double dt, const std::vec
     if (force) volume<T, MODE_STAGE, true>(S, ys, yfp, fh.data(), fld, st, nullptr);
     else volume<T, MODE_STAGE, false>(S, ys, yfp, fh.data(), fld, st, nullptr);
     emu::launch(152, kThreads, 0, [&] {
-      limit_list_kernel<K>(out, list.data(), &S.ctrl.n_flag, S.t64.data(), S.g, &S.ctrl, 1, yfp, nullptr, nullptr);
+      limit_list_kernel<K>(out, list.data(), &S.ctrl.n_flag, S.t64.data(), S.g, &S.ctrl, 1, yfp, nullptr, nullptr,
+                           S.t32.data());
     });
     ys = out;
   }
@@ -289,7 +290,8 @@ static void run_step(Setup& S, std::vector<double>& y, double dt, const std::vec
     energy_reset_kernel<K, T, 32>(y.data(), tabT, S.t64.data(), S.g, rc, part.data(), list.data(), &S.ctrl, yfp);
   });
   emu::launch(152, kThreads, 0, [&] {
-    limit_list_kernel<K>(y.data(), list.data(), &S.ctrl.n_flag, S.t64.data(), S.g, &S.ctrl, 0, yfp, nullptr, nullptr);
+    limit_list_kernel<K>(y.data(), list.data(), &S.ctrl.n_flag, S.t64.data(), S.g, &S.ctrl, 0, yfp, nullptr, nullptr,
+                         S.t32.data());
   });
   double diss = 0.0;
   for (unsigned b = 0; b < nbr; ++b) diss += part[b];
@@ -435,7 +437,7 @@ static int run_limit_project(int argc, char** argv) {
     if (!read_file(argv[8], y.data(), y.size())) return 3;
     std::vector<int8_t> flags(S.nc, -1);
     emu::launch(grid1(S.nc, kThreads), kThreads, 0,
-                [&] { limit_kernel<K>(y.data(), flags.data(), S.t64.data(), S.g, &S.ctrl); });
+                [&] { limit_kernel<K>(y.data(), flags.data(), S.t64.data(), S.g, &S.ctrl, S.t32.data()); });
     FILE* f = std::fopen(argv[10], "wb");
     if (!f) return 3;
     std::fwrite(flags.data(), 1, flags.size(), f);
