@@ -71,6 +71,8 @@ def parse():
     ap.add_argument("--ind-train-n", type=int, default=32)
     ap.add_argument("--ind-train-steps", type=int, default=3000)
     ap.add_argument("--ind-timed-steps", type=int, default=10)
+    ap.add_argument("--ind-network", action="store_true",
+                    help="only time the indicator network's forward and backward kernels on 1M random rows")
     ap.add_argument("--precisions", default="fp64,mixed",
                     help="comma list of fp64,mixed (the first listed of mixed/fp64 is the headline)")
     return ap.parse_args()
@@ -571,6 +573,55 @@ def _ind_init(F, seed):
     return np.concatenate(parts).astype(np.float32)
 
 
+def _ind_network(dgm, torch, order, rows=1 << 20, reps=10):
+    """Forward and backward kernels of the indicator network on `rows` random
+    BF16 feature rows (CUDA events, mean of `reps` launches after 3 warm-up
+    launches of each), with their rooflines: algorithmic HBM bytes (the
+    feature rows read once, the logits or labels) and tensor flops per row
+    (forward F*H + H*H + H MACs; backward the forward again plus dW2, dH1,
+    dW1 and the output layer's gradients), against the measured HBM copy and
+    cuBLAS bf16 peaks."""
+    H = 64
+    nf, F, npar, work = dgm.dg_indicator_sizes(order)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(1)
+    X = torch.randn(rows, F, device="cuda", generator=g).to(torch.bfloat16)
+    y = (torch.rand(rows, device="cuda", generator=g) < 0.1).float()
+    P = torch.from_numpy(_ind_init(F, 3)).cuda()
+    G = torch.zeros(npar + 1, dtype=torch.float32, device="cuda")
+    Wk = torch.empty(work, dtype=torch.uint8, device="cuda")
+    logits = torch.empty(rows, dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        dgm.dg_indicator_forward(order, X, rows, P, logits, 0)
+        dgm.dg_indicator_backward(order, X, y, rows, 1.0, P, G, Wk, work, 0)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev[0].record()
+    for _ in range(reps):
+        dgm.dg_indicator_forward(order, X, rows, P, logits, 0)
+    ev[1].record()
+    for _ in range(reps):
+        dgm.dg_indicator_backward(order, X, y, rows, 1.0, P, G, Wk, work, 0)
+    ev[2].record()
+    torch.cuda.synchronize()
+    fwd_ms, bwd_ms = ev[0].elapsed_time(ev[1]) / reps, ev[1].elapsed_time(ev[2]) / reps
+    pk = measured_peaks()
+    hbm = pk.get("hbm_gbs", 6800.0)
+    tc = pk.get("bf16_tflops", 1900.0)
+    fwd_mac = F * H + H * H + H
+    bwd_mac = fwd_mac + H * H + H * H + F * H + 2 * H
+    out = {"rows": rows, "features": F, "hidden": H, "kernel": "mma.sync m16n8k16 bf16, fp32 accumulate"}
+    for name, ms, mac in (("forward", fwd_ms, fwd_mac), ("backward", bwd_ms, bwd_mac)):
+        byts = rows * (2 * F + 4)
+        flops = rows * 2 * mac
+        t_hbm, t_tc = byts / (hbm * 1e9), flops / (tc * 1e12)
+        out[name] = {"ms": ms, "bytes": byts, "flops": flops, "gbs": byts / (ms * 1e6),
+                     "tflops": flops / (ms * 1e9), "bound": "hbm" if t_hbm >= t_tc else "tensor",
+                     "frac": max(t_hbm, t_tc) / (ms * 1e-3),
+                     "peaks": f"HBM {hbm} GB/s, bf16 {tc} TFLOP/s (measured)"}
+    return out
+
+
 def run_indicator(args):
     """Config 5: the BF16 troubled-cell network trained on the GPU by the
     library's backward and Adam kernels from plain-indicator labels of 32^3
@@ -632,7 +683,7 @@ def run_indicator(args):
     out = {"metric": "learned troubled-cell indicator at 128^3, order 3 (config 5)", "n": n, "order": order,
            "train": {"n": n_tr, "rows": rows_tr, "adam_steps": args.ind_train_steps, "loss_first_last": losses,
                      "seconds": train_s, "pos_weight": pw},
-           "threshold": thr, "workloads": {}}
+           "threshold": thr, "network": _ind_network(dgm, torch, order), "workloads": {}}
     for kind, seed, mach in (("supersonic turbulence, rms Mach 2.5 (seed 7)", 7, 2.5),
                              ("Sod tube (seed 5)", 5, 0.0)):
         fn = syn.supersonic_velocity(seed, mach, GAMMA) if mach > 0 else syn.sod_tube(seed, GAMMA)[0]
@@ -770,6 +821,12 @@ def main():
         args.err_steps = 200 if args.order <= 3 else 100
     if args.sweep:
         run_sweep(args)
+        return
+    if args.ind_network:
+        import torch
+        import paper_1602_09079_gb300 as dgm
+        dgm.load()
+        print(json.dumps(_ind_network(dgm, torch, 3)))
         return
     if args.indicator:
         run_indicator(args)

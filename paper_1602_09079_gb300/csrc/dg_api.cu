@@ -561,11 +561,13 @@ int fused_step(dg_ctx* c, double dt, bool force) {
                                  c->ind_logit_thr, c->list2, &c->ctrl->n_gate, &c->ctrl->n_queued_total, c->stream);
       }));
       DG_TRY(launch(c, KC_LIMIT, [&] {
-        return c->fn.limit_list(out, c->list2, &c->ctrl->n_gate, c->geo, c->ctrl, 0, yf, y0, dinc, c->stream);
+        return c->fn.limit_list(out, c->list2, &c->ctrl->n_gate, c->geo, c->ctrl, 0, yf, y0, dinc, c->list,
+                                c->stream);
       }));
     } else {
       DG_TRY(launch(c, KC_LIMIT, [&] {
-        return c->fn.limit_list(out, c->list, &c->ctrl->n_flag, c->geo, c->ctrl, 1, yf, y0, dinc, c->stream);
+        return c->fn.limit_list(out, c->list, &c->ctrl->n_flag, c->geo, c->ctrl, 1, yf, y0, dinc, c->list2,
+                                c->stream);
       }));
     }
     ys = out;
@@ -839,12 +841,13 @@ int dg_step(dg_ctx* c, double dt) {
                                  c->ind_logit_thr, c->list2, &c->ctrl->n_gate, &c->ctrl->n_queued_total, c->stream);
       }));
       DG_TRY(launch(c, KC_LIMIT, [&] {
-        return c->fn.limit_list(out, c->list2, &c->ctrl->n_gate, c->geo, c->ctrl, 0, yf, nullptr, nullptr,
+        return c->fn.limit_list(out, c->list2, &c->ctrl->n_gate, c->geo, c->ctrl, 0, yf, nullptr, nullptr, c->list,
                                 c->stream);
       }));
     } else {
       DG_TRY(launch(c, KC_LIMIT, [&] {
-        return c->fn.limit_list(out, c->list, &c->ctrl->n_flag, c->geo, c->ctrl, 1, yf, nullptr, nullptr, c->stream);
+        return c->fn.limit_list(out, c->list, &c->ctrl->n_flag, c->geo, c->ctrl, 1, yf, nullptr, nullptr, c->list2,
+                                c->stream);
       }));
     }
     ys = out;
@@ -963,7 +966,8 @@ int dg_energy_reset(dg_ctx* c, double c_iso, double rho0, double* dissipated) {
   // the positivity limiter after the reset (Sect. 3.2): full limiter on the
   // cells that failed the screen
   DG_TRY(launch(c, KC_RESET, [&] {
-    return c->fn.limit_list(c->y, c->list, &c->ctrl->n_flag, c->geo, c->ctrl, 0, yf, nullptr, nullptr, c->stream);
+    return c->fn.limit_list(c->y, c->list, &c->ctrl->n_flag, c->geo, c->ctrl, 0, yf, nullptr, nullptr, c->list2,
+                                c->stream);
   }));
   c->limited = true;
   if (dissipated) {

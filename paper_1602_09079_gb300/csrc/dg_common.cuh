@@ -101,7 +101,7 @@ struct Ctrl {
   unsigned int n_flag;              // cells queued for the full limiter
   unsigned long long n_limited;     // limiter count
   unsigned int n_gate;              // queued cells the indicator passes on
-  unsigned int pad2;
+  unsigned int n_deep;              // queued cells the FP32 point screen does not clear
   unsigned long long n_queued_total;  // cells that failed the limiter screen (all stages)
   unsigned long long n_full_total;    // cells that went through the full limiter
   double pad1[2];
@@ -513,13 +513,66 @@ __device__ bool point_screen_f32(const double* w, long long stride, const float*
   return true;
 }
 
+// The cheap part of the Zhang-Shu limiter of one cell (Sect. 2.5) on its 5N
+// FP64 coefficients w[(i*N + l) * stride]: the means (finite, positive:
+// otherwise an error bit is ORed into err and false returned), the
+// excursion bounds sabs_i = sum_{l>=1} |w_il| max |phi_l| and the modal
+// sufficient tests (mean minus sabs with a rounding margin) for the density
+// (rho_safe) and the pressure (p_safe; needs rho_safe). When both hold, or
+// (tab32 != nullptr) the FP32 point screen (point_screen_f32) holds, the
+// limiter provably leaves the cell unchanged and *none is set.
+template <int K>
+__device__ bool limit_prelude(const double* w, long long stride, const double* __restrict__ tab, double gamma,
+                              double eps_r, double eps_p, unsigned* err, int vol, const float* __restrict__ tab32,
+                              double* mean, double* sabs, bool* rho_safe, bool* p_safe, bool* none) {
+  using TB = Tab<K>;
+  constexpr int N = TB::N;
+  const double gm1 = gamma - 1.0;
+  bool finite = true;
+#pragma unroll
+  for (int i = 0; i < 5; ++i) mean[i] = w[(i * N) * stride];
+  for (int j = 0; j < 5 * N; ++j) finite &= isfinite(w[j * stride]);
+  if (!finite) {
+    *err |= ERRB_NONFINITE;
+    return false;
+  }
+  const double pbar = gm1 * (mean[4] - 0.5 * (mean[1] * mean[1] + mean[2] * mean[2] + mean[3] * mean[3]) / mean[0]);
+  if (!(mean[0] >= eps_r) || !(pbar >= eps_p)) {
+    *err |= ERRB_POSITIVITY;
+    return false;
+  }
+  if (N == 1) return false;
+  const double* lmax = tab + (vol ? TB::LMAXV : TB::LMAX);
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    double s = 0.0;
+    for (int l = 1; l < N; ++l) s += fabs(w[(i * N + l) * stride]) * __ldg(lmax + l);
+    sabs[i] = s;
+  }
+  const double rlo = mean[0] - sabs[0];
+  *rho_safe = rlo >= eps_r + 1e-13 * (fabs(mean[0]) + sabs[0]);
+  *p_safe = false;
+  if (*rho_safe) {
+    const double elo = mean[4] - sabs[4];
+    double kin = 0.0;
+#pragma unroll
+    for (int a = 1; a <= 3; ++a) {
+      const double mh = fabs(mean[a]) + sabs[a];
+      kin += mh * mh;
+    }
+    kin *= 0.5 / rlo;
+    *p_safe = gm1 * (elo - kin) >= eps_p + 1e-13 * gm1 * (fabs(mean[4]) + sabs[4] + kin);
+  }
+  *none = (*rho_safe && *p_safe) ||
+          (tab32 && point_screen_f32<K>(w, stride, tab32, mean, sabs, gamma, eps_r, eps_p, vol));
+  return true;
+}
+
 // Zhang-Shu positivity limiter of one cell (Sect. 2.5) on its 5N FP64
-// coefficients w[(i*N + l) * stride]. A cheap sufficient test (mean minus
-// the sum of |w_l| max_S |phi_l|, with a rounding margin) skips the point
-// evaluations when the limiter provably leaves the cell unchanged; with an
-// FP32 table (tab32 != nullptr) the FP32 point screen (point_screen_f32)
-// follows before the FP64 point evaluations.
-// Returns flag bits (1: theta1 < 1, 2: theta2 < 1) and ORs errors into err.
+// coefficients w[(i*N + l) * stride]: limit_prelude's sufficient tests skip
+// the FP64 point evaluations when the limiter provably leaves the cell as it
+// is. Returns flag bits (1: theta1 < 1, 2: theta2 < 1) and ORs errors into
+// err.
 template <int K>
 __device__ int limit_cell(double* w, long long stride, const double* __restrict__ tab, double gamma,
                           double eps_r, double eps_p, unsigned* err, int vol,
@@ -527,55 +580,18 @@ __device__ int limit_cell(double* w, long long stride, const double* __restrict_
   using TB = Tab<K>;
   constexpr int N = TB::N;
   const double gm1 = gamma - 1.0;
-  double mean[5];
-  bool finite = true;
-#pragma unroll
-  for (int i = 0; i < 5; ++i) mean[i] = w[(i * N) * stride];
-  for (int j = 0; j < 5 * N; ++j) finite &= isfinite(w[j * stride]);
-  if (!finite) {
-    *err |= ERRB_NONFINITE;
+  double mean[5], sabs[5];
+  bool rho_safe, p_safe, none;
+  if (!limit_prelude<K>(w, stride, tab, gamma, eps_r, eps_p, err, vol, tab32, mean, sabs, &rho_safe, &p_safe,
+                        &none) ||
+      none)
     return 0;
-  }
-  double pbar = gm1 * (mean[4] - 0.5 * (mean[1] * mean[1] + mean[2] * mean[2] + mean[3] * mean[3]) / mean[0]);
-  if (!(mean[0] >= eps_r) || !(pbar >= eps_p)) {
-    *err |= ERRB_POSITIVITY;
-    return 0;
-  }
-  if (N == 1) return 0;
-  const double* lmax = tab + (vol ? TB::LMAXV : TB::LMAX);
   const double* lphi = tab + TB::LPHI;
   const double* vphi = tab + TB::VPHI;
   // the point set: S (TB::NL points), then optionally the volume Gauss points
   const int npts = TB::NL + (vol ? TB::Q3 : 0);
-  double sabs[5];
-#pragma unroll
-  for (int i = 0; i < 5; ++i) {
-    double s = 0.0;
-    for (int l = 1; l < N; ++l) s += fabs(w[(i * N + l) * stride]) * __ldg(lmax + l);
-    sabs[i] = s;
-  }
   int flag = 0;
   // density: theta1
-  double rlo = mean[0] - sabs[0];
-  bool rho_safe = rlo >= eps_r + 1e-13 * (fabs(mean[0]) + sabs[0]);
-  if (tab32) {
-    // the modal pressure bound (as below); when both modal bounds hold the
-    // point evaluations below are skipped anyway
-    bool p_modal = false;
-    if (rho_safe) {
-      const double elo = mean[4] - sabs[4];
-      double kin = 0.0;
-#pragma unroll
-      for (int a = 1; a <= 3; ++a) {
-        const double mh = fabs(mean[a]) + sabs[a];
-        kin += mh * mh;
-      }
-      kin *= 0.5 / rlo;
-      p_modal = gm1 * (elo - kin) >= eps_p + 1e-13 * gm1 * (fabs(mean[4]) + sabs[4] + kin);
-    }
-    if (!(rho_safe && p_modal) && point_screen_f32<K>(w, stride, tab32, mean, sabs, gamma, eps_r, eps_p, vol))
-      return 0;
-  }
   if (!rho_safe) {
     double rmin = mean[0];
     for (int s = 0; s < npts; ++s) {
@@ -593,20 +609,8 @@ __device__ int limit_cell(double* w, long long stride, const double* __restrict_
       }
     }
   }
-  // pressure: theta2
-  bool p_safe = false;
-  if (rho_safe) {
-    double elo = mean[4] - sabs[4];
-    double kin = 0.0;
-#pragma unroll
-    for (int a = 1; a <= 3; ++a) {
-      double mh = fabs(mean[a]) + sabs[a];
-      kin += mh * mh;
-    }
-    kin *= 0.5 / rlo;
-    double plo = gm1 * (elo - kin);
-    p_safe = plo >= eps_p + 1e-13 * gm1 * (fabs(mean[4]) + sabs[4] + kin);
-  }
+  // pressure: theta2 (the prelude's modal test p_safe holds only where
+  // rho_safe did, i.e. where theta1 left the cell unchanged)
   if (!p_safe) {
     double th2 = 1.0;
     bool newton_fail = false;

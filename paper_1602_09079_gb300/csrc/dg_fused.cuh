@@ -406,16 +406,7 @@ __global__ void __launch_bounds__(FusedCfg<K>::THREADS, FusedCfg<K>::MINB) fused
   const int gx = x0 + cx, gy = y0 + cy;
   const long long nc = g.nc;
   const float gm1 = (float)(g.gamma - 1.0), gam = (float)g.gamma;
-  // flux scalings 1/(4 dx_d): every volume and face flux term is kept in
-  // units of the x scaling s0 (relative factors rel[d], exactly 1 on cubic
-  // cells, where the multiplies are skipped), the source is divided by s0,
-  // and s0 is applied once per coefficient in the stage update (P4)
-  const float s0 = (float)(0.25 * g.inv_dx[0]);
-  const float rel[3] = {1.f, (float)(0.25 * g.inv_dx[1]) / s0, (float)(0.25 * g.inv_dx[2]) / s0};
-  const bool aniso = rel[1] != 1.f || rel[2] != 1.f;
-  const float src_scale = 0.125f / s0;
-  const float b0dt_s = a.b0dt * s0;
-  const double b0dt_sd = a.b0dt_d * (double)s0;
+  const float scale[3] = {(float)(0.25 * g.inv_dx[0]), (float)(0.25 * g.inv_dx[1]), (float)(0.25 * g.inv_dx[2])};
   // slots of this cell's high x and y faces
   const int hx = cx + 1 < vx ? c + 1 : NC + cy;
   const int hy = cy + 1 < vy ? c + BX : NC + cx;
@@ -528,7 +519,7 @@ __global__ void __launch_bounds__(FusedCfg<K>::THREADS, FusedCfg<K>::MINB) fused
           o = (it / SX) * SZ + slot;
           oL = CF::XL;
           oR = CF::XR;
-          sc = rel[0];
+          sc = scale[0];
           valid = slot < NC ? ((slot % BX) < vx && (slot / BX) < vy) : slot - NC < vy;
         } else if (it < (SX + SY) * Q2) {
           const int r = it - SX * Q2;
@@ -536,7 +527,7 @@ __global__ void __launch_bounds__(FusedCfg<K>::THREADS, FusedCfg<K>::MINB) fused
           o = (r / SY) * SZ + slot;
           oL = CF::YL;
           oR = CF::YR;
-          sc = rel[1];
+          sc = scale[1];
           valid = slot < NC ? ((slot % BX) < vx && (slot / BX) < vy) : slot - NC < vx;
         } else {
           const int r = it - (SX + SY) * Q2;
@@ -544,7 +535,7 @@ __global__ void __launch_bounds__(FusedCfg<K>::THREADS, FusedCfg<K>::MINB) fused
           o = (r / NC) * SZ + slot;
           oL = CF::ZL;
           oR = CF::ZR;
-          sc = rel[2];
+          sc = scale[2];
           valid = (slot % BX) < vx && (slot / BX) < vy;
         }
         if (valid) {
@@ -559,12 +550,8 @@ __global__ void __launch_bounds__(FusedCfg<K>::THREADS, FusedCfg<K>::MINB) fused
             UR[v] = pr[v * Q2 * SZ];
           }
           err |= face_flux_x<FLUX>(UL, UR, gam, F);
-          if (aniso) {
 #pragma unroll
-            for (int v = 0; v < 5; ++v) F[v] *= sc;
-          }
-#pragma unroll
-          for (int v = 0; v < 5; ++v) pr[v * Q2 * SZ] = F[v];
+          for (int v = 0; v < 5; ++v) pr[v * Q2 * SZ] = F[v] * sc;
         }
       }
     }
@@ -591,7 +578,7 @@ __global__ void __launch_bounds__(FusedCfg<K>::THREADS, FusedCfg<K>::MINB) fused
         if (a.stage == 0) {
           double* pr = a.R + o0;
 #pragma unroll
-          for (int l = 0; l < N; ++l, pr += rs) *pr = (l == 0 && i == 0) ? -(double)s0 * accm : f32_to_f64_q(-s0 * acc[l]);
+          for (int l = 0; l < N; ++l, pr += rs) *pr = (l == 0 && i == 0) ? -accm : f32_to_f64_q(-acc[l]);
         } else {
           float sab = 0.f;
           double mean = 0.0;
@@ -607,10 +594,10 @@ __global__ void __launch_bounds__(FusedCfg<K>::THREADS, FusedCfg<K>::MINB) fused
               // b0 y_s + b0 dt dw/dt, with dw/dt from the FP64 face sum (y_0
               // is read for this one value per cell; in stage 1 y_0 = y_s)
               const double y00 = a.stage >= 2 ? a.y0[o] : ysv;
-              v = fma(a.a0_d, y00, fma(a.b0_d, ysv, b0dt_sd * accm));
+              v = fma(a.a0_d, y00, fma(a.b0_d, ysv, a.b0dt_d * accm));
               dnew = f64_to_f32_q(v - y00);
             } else {
-              const float delta = fmaf(b0dt_s, acc[l], -a.a0 * dl);
+              const float delta = fmaf(a.b0dt, acc[l], -a.a0 * dl);
               v = ysv + f32_to_f64_q(delta);
               dnew = dl + delta;
             }
@@ -763,19 +750,13 @@ __global__ void __launch_bounds__(FusedCfg<K>::THREADS, FusedCfg<K>::MINB) fused
                 float F[5];
                 euler_flux<float>(dd, U, vel, p, F);
 #pragma unroll
-                if (aniso) {
-#pragma unroll
-                  for (int v = 0; v < 5; ++v) F[v] *= rel[dd];
-                }
-#pragma unroll
-                for (int v = 0; v < 5; ++v) sm[CF::VF + ((dd * 5 + v) * Q2 + qs) * NC + cc] = F[v];
+                for (int v = 0; v < 5; ++v) sm[CF::VF + ((dd * 5 + v) * Q2 + qs) * NC + cc] = F[v] * scale[dd];
               }
               if (FORCE) {
-                const float rs8 = src_scale * U[0];
-                sm[CF::VS + (0 * Q2 + qs) * NC + cc] = rs8 * ac[k][0];
-                sm[CF::VS + (1 * Q2 + qs) * NC + cc] = rs8 * ac[k][1];
-                sm[CF::VS + (2 * Q2 + qs) * NC + cc] = rs8 * ac[k][2];
-                sm[CF::VS + (3 * Q2 + qs) * NC + cc] = src_scale * (U[1] * ac[k][0] + U[2] * ac[k][1] + U[3] * ac[k][2]);
+                sm[CF::VS + (0 * Q2 + qs) * NC + cc] = 0.125f * U[0] * ac[k][0];
+                sm[CF::VS + (1 * Q2 + qs) * NC + cc] = 0.125f * U[0] * ac[k][1];
+                sm[CF::VS + (2 * Q2 + qs) * NC + cc] = 0.125f * U[0] * ac[k][2];
+                sm[CF::VS + (3 * Q2 + qs) * NC + cc] = 0.125f * (U[1] * ac[k][0] + U[2] * ac[k][1] + U[3] * ac[k][2]);
               }
             }
           }

@@ -97,7 +97,11 @@ cudaError_t upload(const double* h64, const float* h32) {
   h_tab64[dev] = static_cast<const double*>(p);
   if ((e = cudaGetSymbolAddress(&p, g_tab32)) != cudaSuccess) return e;
   h_tab32[dev] = static_cast<const float*>(p);
-  cudaError_t r = cudaSuccess;
+  cudaError_t r = cudaFuncSetAttribute(limit_list_kernel<KK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)ListLim<KK>::smem());
+  if (r == cudaSuccess)
+    r = cudaFuncSetAttribute(limit_screen_list_kernel<KK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)ListLim<KK>::smem());
   if constexpr (kRegF32) {
     cudaError_t f[4] = {set_f32_smem_fw<MODE_RHS, false>(), set_f32_smem_fw<MODE_RHS, true>(),
                         set_f32_smem_fw<MODE_STAGE, false>(), set_f32_smem_fw<MODE_STAGE, true>()};
@@ -200,9 +204,15 @@ cudaError_t volume_stage(int prec, bool force, const void* fh, const void* field
 }
 
 cudaError_t limit_list(double* y, const int* list, const unsigned* count, const Geo& g, Ctrl* ctrl, int count_queued,
-                       float* yf, const double* y0, float* d, cudaStream_t s) {
-  limit_list_kernel<KK><<<152, kThreads, 0, s>>>(y, list, count, tab_ptr<double>(), g, ctrl, count_queued, yf, y0, d,
-                                                  tab_ptr<float>());
+                       float* yf, const double* y0, float* d, int* deep, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(&ctrl->n_deep, 0, sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  using LL = ListLim<KK>;
+  limit_screen_list_kernel<KK><<<152 * LL::MINB, LL::THREADS, LL::smem(), s>>>(
+      y, list, count, tab_ptr<double>(), tab_ptr<float>(), g, ctrl, count_queued, deep);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  limit_list_kernel<KK><<<152 * LL::MINB, LL::THREADS, LL::smem(), s>>>(y, deep, &ctrl->n_deep, tab_ptr<double>(), g,
+                                                                       ctrl, yf, y0, d);
   return cudaGetLastError();
 }
 
@@ -217,9 +227,7 @@ cudaError_t limit(double* y, int8_t* flags, const Geo& g, Ctrl* ctrl, cudaStream
 }
 
 cudaError_t cfl(const double* y, const Geo& g, Ctrl* ctrl, cudaStream_t s) {
-  unsigned nb = grid1(g.nc, kThreads);
-  if (nb > 152u * 8u) nb = 152u * 8u;
-  cfl_kernel<KK><<<nb, kThreads, 0, s>>>(y, g, ctrl);
+  cfl_kernel<KK><<<grid1(g.nc, kThreads), kThreads, 0, s>>>(y, g, ctrl);
   return cudaGetLastError();
 }
 

@@ -695,28 +695,74 @@ __global__ void __launch_bounds__(VolF32<K>::THREADS, VolF32<K>::MINB) volume_f3
 }
 
 // Full positivity limiter on the cells queued by a stage kernel (list of
-// *count cells).
+// *count cells), in two passes, one thread per cell. The first
+// (limit_screen_list_kernel) runs limit_cell's sufficient tests, the modal
+// bounds and then the FP32 point screen; the cells that fail both go to a
+// second list (*n_deep), which the second pass (limit_list_kernel) limits
+// with the FP64 point evaluations. A cell's FP64 points run in one thread on the FP64
+// pipe, so compacting these cells keeps its warps full (in the first pass
+// one troubled cell among 32 would hold up the FP64 pipe for the whole
+// warp). Each thread copies its cell's 5N coefficients to shared memory once
+// and works on them there: the tests and the point evaluations read every
+// coefficient several times (once per point), and from global memory the
+// scattered cells of a warp would pull a 128-byte line per coefficient and
+// thread through L1 again at every read. Limited cells are written back.
 template <int K>
-__global__ void __launch_bounds__(kThreads) limit_list_kernel(double* __restrict__ y, const int* __restrict__ list,
-                                                              const unsigned* count, const double* __restrict__ tab64,
-                                                              Geo g, Ctrl* ctrl, int count_queued,
-                                                              float* __restrict__ yf, const double* __restrict__ y0,
-                                                              float* __restrict__ dinc, const float* __restrict__ tab32) {
-  constexpr int N = nmodes(K);
+struct ListLim {
+  static constexpr int N = nmodes(K);
+  static constexpr int THREADS = 128;
+  static constexpr int MINB = K >= 3 ? 2 : 4;  // 5 N doubles per thread: 100 KB per block at degree 3
+  static constexpr size_t smem() { return (size_t)5 * N * THREADS * sizeof(double); }
+};
+
+template <int K>
+__global__ void __launch_bounds__(ListLim<K>::THREADS, ListLim<K>::MINB)
+    limit_screen_list_kernel(const double* __restrict__ y, const int* __restrict__ list, const unsigned* count,
+                             const double* __restrict__ tab64, const float* __restrict__ tab32, Geo g, Ctrl* ctrl,
+                             int count_queued, int* __restrict__ deep) {
+  constexpr int N = nmodes(K), LT = ListLim<K>::THREADS;
+  extern __shared__ __align__(16) double ws[];
   const unsigned n = *count;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     atomicAdd(&ctrl->n_full_total, (unsigned long long)n);
     if (count_queued) atomicAdd(&ctrl->n_queued_total, (unsigned long long)n);
   }
   unsigned e = 0;
-  for (unsigned i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) {
+  double* w = ws + threadIdx.x;  // this thread's column, stride LT
+  for (unsigned i = blockIdx.x * LT + threadIdx.x; i < n; i += gridDim.x * LT) {
+    const int cell = list[i];
+    for (int r = 0; r < 5 * N; ++r) w[r * LT] = y[(size_t)r * g.nc + cell];
+    double mean[5], sabs[5];
+    bool rho_safe, p_safe, none;
+    if (limit_prelude<K>(w, LT, tab64, g.gamma, g.eps_rho, g.eps_p, &e, g.lim_vol, tab32, mean, sabs, &rho_safe,
+                         &p_safe, &none) &&
+        !none)
+      deep[atomicAdd(&ctrl->n_deep, 1u)] = cell;
+  }
+  if (e) atomicOr(&ctrl->err, e);
+}
+
+template <int K>
+__global__ void __launch_bounds__(ListLim<K>::THREADS, ListLim<K>::MINB)
+    limit_list_kernel(double* __restrict__ y, const int* __restrict__ list, const unsigned* count,
+                      const double* __restrict__ tab64, Geo g, Ctrl* ctrl, float* __restrict__ yf,
+                      const double* __restrict__ y0, float* __restrict__ dinc) {
+  constexpr int N = nmodes(K), LT = ListLim<K>::THREADS;
+  extern __shared__ __align__(16) double ws[];
+  const unsigned n = *count;
+  unsigned e = 0;
+  double* w = ws + threadIdx.x;  // this thread's column, stride LT
+  for (unsigned i = blockIdx.x * LT + threadIdx.x; i < n; i += gridDim.x * LT) {
     const long long cell = list[i];
-    if (limit_cell<K>(y + cell, g.nc, tab64, g.gamma, g.eps_rho, g.eps_p, &e, g.lim_vol, tab32)) {
-      if (yf)
-        for (int r = 0; r < 5 * N; ++r) yf[(size_t)r * g.nc + cell] = (float)y[(size_t)r * g.nc + cell];
-      if (dinc)
-        for (int r = 0; r < 5 * N; ++r)
-          dinc[(size_t)r * g.nc + cell] = (float)(y[(size_t)r * g.nc + cell] - y0[(size_t)r * g.nc + cell]);
+    const long long nc = g.nc;
+    for (int r = 0; r < 5 * N; ++r) w[r * LT] = y[(size_t)r * nc + cell];
+    if (limit_cell<K>(w, LT, tab64, g.gamma, g.eps_rho, g.eps_p, &e, g.lim_vol)) {
+      for (int r = 0; r < 5 * N; ++r) {
+        const double v = w[r * LT];
+        y[(size_t)r * nc + cell] = v;
+        if (yf) yf[(size_t)r * nc + cell] = (float)v;
+        if (dinc) dinc[(size_t)r * nc + cell] = (float)(v - y0[(size_t)r * nc + cell]);
+      }
     }
   }
   if (e) atomicOr(&ctrl->err, e);
@@ -1377,37 +1423,71 @@ __global__ void __launch_bounds__(kThreads) limit_kernel(double* __restrict__ y,
 }
 
 // ------------------------------------------------------------ CFL (max s)
-// s_K = sum_a (|v_a| + c) / dx_a from the cell means; max over cells by a
-// warp-shuffle / shared-memory / one-atomic-per-block reduction on the bit
-// pattern of the non-negative double.
+// s_K = sum_a (|v_a| + c) / dx_a from the cell means; the result is the FP64
+// maximum over cells, bit for bit what the plain FP64 loop gives, but the
+// FP64 division and square root (the FP64 pipe is about 1/64 of the FP32
+// rate) run for a few cells per block only. One cell per thread: s in FP32
+// first (means converted on the integer pipe, correctly rounded reciprocal
+// and square root), then the block's FP32 maximum over the trusted cells; the cells
+// within a relative 1e-3 of it and the untrusted ones (means not finite or
+// not clearly positive, pressure from a cancellation E - kin with kin above
+// 0.99 E) are evaluated in FP64, and the FP64 maximum of those is the
+// block's maximum. A trusted cell's FP32 s is within a relative 1e-4 of its
+// FP64 s (a few roundings, the pressure's amplified at most 199x by the
+// cancellation, halved by the square root), so the cell holding the
+// block's FP64 maximum is always among the re-evaluated ones. Blocks combine
+// by one atomicMax on the bit pattern of the non-negative double.
 template <int K>
 __global__ void __launch_bounds__(kThreads) cfl_kernel(const double* __restrict__ y, Geo g, Ctrl* ctrl) {
   constexpr int N = nmodes(K);
   const long long nc = g.nc;
+  const long long c = (long long)blockIdx.x * kThreads + threadIdx.x;
+  double r = 1.0, m1 = 0.0, m2 = 0.0, m3 = 0.0, E = 0.0;
+  float sf = 0.f;
+  bool trusted = false;
+  if (c < nc) {
+    r = y[c];
+    m1 = y[(size_t)N * nc + c];
+    m2 = y[(size_t)2 * N * nc + c];
+    m3 = y[(size_t)3 * N * nc + c];
+    E = y[(size_t)4 * N * nc + c];
+    const float rf = f64_to_f32(r), m1f = f64_to_f32(m1), m2f = f64_to_f32(m2), m3f = f64_to_f32(m3);
+    const float Ef = f64_to_f32(E);
+    const float irf = __frcp_rn(rf);
+    const float kin = 0.5f * (m1f * m1f + m2f * m2f + m3f * m3f) * irf;
+    const float prf = f64_to_f32(g.gamma - 1.0) * (Ef - kin);
+    const float csf = sqrtf(f64_to_f32(g.gamma) * prf * irf);
+    sf = (fabsf(m1f) * irf + csf) * f64_to_f32(g.inv_dx[0]) + (fabsf(m2f) * irf + csf) * f64_to_f32(g.inv_dx[1]) +
+         (fabsf(m3f) * irf + csf) * f64_to_f32(g.inv_dx[2]);
+    trusted = rf >= 1e-30f && rf <= 1e30f && Ef <= 1e30f && kin <= 0.99f * Ef && prf >= 1e-30f && sf <= 3e38f;
+  }
+  __shared__ float s_wf[kThreads / 32];
+  __shared__ double s_w[kThreads / 32];
+  __shared__ unsigned s_err;
+  float mf = trusted ? sf : 0.f;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mf = fmaxf(mf, __shfl_xor_sync(0xffffffffu, mf, o));
+  if (threadIdx.x == 0) s_err = 0u;
+  if ((threadIdx.x & 31) == 0) s_wf[threadIdx.x >> 5] = mf;
+  __syncthreads();
+  mf = s_wf[0];
+#pragma unroll
+  for (int w = 1; w < kThreads / 32; ++w) mf = fmaxf(mf, s_wf[w]);
   double smax = 0.0;
   unsigned e = 0;
-  for (long long c = (long long)blockIdx.x * kThreads + threadIdx.x; c < nc; c += (long long)gridDim.x * kThreads) {
-    const double r = y[c];
-    const double m1 = y[(size_t)N * nc + c], m2 = y[(size_t)2 * N * nc + c], m3 = y[(size_t)3 * N * nc + c];
-    const double E = y[(size_t)4 * N * nc + c];
-    // one division and one square root per cell (the FP64 pipe is the bound)
+  if (c < nc && (!trusted || sf >= mf * (1.f - 1e-3f))) {
     const double ir = 1.0 / r;
     const double pr = (g.gamma - 1.0) * (E - 0.5 * (m1 * m1 + m2 * m2 + m3 * m3) * ir);
     if (!(r > 0.0) || !(pr > 0.0)) {
-      e |= (isfinite(r) && isfinite(pr)) ? ERRB_POSITIVITY : ERRB_NONFINITE;
-      continue;
+      e = (isfinite(r) && isfinite(pr)) ? ERRB_POSITIVITY : ERRB_NONFINITE;
+    } else {
+      const double cs = sqrt(g.gamma * pr * ir);
+      smax = (fabs(m1) * ir + cs) * g.inv_dx[0] + (fabs(m2) * ir + cs) * g.inv_dx[1] +
+             (fabs(m3) * ir + cs) * g.inv_dx[2];
     }
-    const double cs = sqrt(g.gamma * pr * ir);
-    const double s = (fabs(m1) * ir + cs) * g.inv_dx[0] + (fabs(m2) * ir + cs) * g.inv_dx[1] +
-                     (fabs(m3) * ir + cs) * g.inv_dx[2];
-    smax = fmax(smax, s);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o));
-  __shared__ double s_w[kThreads / 32];
-  __shared__ unsigned s_err;
-  if (threadIdx.x == 0) s_err = 0u;
-  __syncthreads();
   if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = smax;
   if (e) atomicOr(&s_err, e);
   __syncthreads();

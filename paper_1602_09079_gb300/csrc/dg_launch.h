@@ -34,9 +34,11 @@ struct Launchers {
   // to the screen-failure total, i.e. no indicator filtered the list); yf
   // (nullable): FP32 shadow updated for the cells the limiter changes; d
   // (nullable): the fused stage kernels' FP32 increment y - y0 of the step,
-  // recomputed for the cells the limiter changes
+  // recomputed for the cells the limiter changes; deep: scratch list of
+  // g.nc entries (not list) for the cells that need the FP64 point
+  // evaluations (ctrl->n_deep)
   cudaError_t (*limit_list)(double* y, const int* list, const unsigned* count, const Geo& g, Ctrl* ctrl,
-                            int count_queued, float* yf, const double* y0, float* d, cudaStream_t s);
+                            int count_queued, float* yf, const double* y0, float* d, int* deep, cudaStream_t s);
   // screen[c] = 1 if cell c fails the limiter screen
   cudaError_t (*screen)(const double* y, uint8_t* screen, const Geo& g, cudaStream_t s);
   cudaError_t (*limit)(double* y, int8_t* flags, const Geo& g, Ctrl* ctrl, cudaStream_t s);

@@ -206,6 +206,21 @@ static void run_rhs(Setup& S, std::vector<double>& y, std::vector<double>& R) {
   std::printf("err=%u dissipated=0 smax=0\n", S.ctrl.err);
 }
 
+// the full limiter on the queued cells as the C ABI runs it: the screen pass
+// queues the cells that need the FP64 point evaluations into deep, the
+// second pass limits them
+static void limit_queued(Setup& S, double* y, const int* list, int count_queued, float* yf, const double* y0,
+                         float* dinc, std::vector<int>& deep) {
+  S.ctrl.n_deep = 0;
+  emu::launch(4, ListLim<K>::THREADS, ListLim<K>::smem(), [&] {
+    limit_screen_list_kernel<K>(y, list, &S.ctrl.n_flag, S.t64.data(), S.t32.data(), S.g, &S.ctrl, count_queued,
+                                deep.data());
+  });
+  emu::launch(4, ListLim<K>::THREADS, ListLim<K>::smem(), [&] {
+    limit_list_kernel<K>(y, deep.data(), &S.ctrl.n_deep, S.t64.data(), S.g, &S.ctrl, yf, y0, dinc);
+  });
+}
+
 template <typename T>
 static void run_step(Setup& S, std::vector<double>& y, double dt, const std::vector<double>& modes, int nm,
                      double c_iso, double rho0) {
@@ -226,7 +241,7 @@ static void run_step(Setup& S, std::vector<double>& y, double dt, const std::vec
   float* yfp = shadow ? yf.data() : nullptr;
   std::vector<T> fh((size_t)15 * TB::Q2 * nc, T(std::nan("")));
   std::vector<double> ybuf(y.size(), std::nan(""));
-  std::vector<int> list(nc, -1);
+  std::vector<int> list(nc, -1), deep(nc, -1);
   const double a0[3] = {0.0, 0.75, 1.0 / 3.0}, b0[3] = {1.0, 0.25, 2.0 / 3.0};
   const double* ys = y.data();
 #if DG_K >= 2
@@ -255,10 +270,8 @@ static void run_step(Setup& S, std::vector<double>& y, double dt, const std::vec
       S.ctrl.n_flag = 0;
       if (force) fused_launch<true>(S, a);
       else fused_launch<false>(S, a);
-      emu::launch(152, kThreads, 0, [&] {
-        limit_list_kernel<K>(out, list.data(), &S.ctrl.n_flag, S.t64.data(), S.g, &S.ctrl, 1, s == 2 ? yfp : nullptr,
-                             s < 2 ? y.data() : nullptr, s < 2 ? dinc.data() : nullptr, S.t32.data());
-      });
+      limit_queued(S, out, list.data(), 1, s == 2 ? yfp : nullptr, s < 2 ? y.data() : nullptr,
+                   s < 2 ? dinc.data() : nullptr, deep);
       ys = out;
     }
   } else
@@ -270,10 +283,7 @@ static void run_step(Setup& S, std::vector<double>& y, double dt, const std::vec
     StageArgs st{ys, y.data(), out, a0[s], b0[s], dt, list.data(), yfp};
     if (force) volume<T, MODE_STAGE, true>(S, ys, yfp, fh.data(), fld, st, nullptr);
     else volume<T, MODE_STAGE, false>(S, ys, yfp, fh.data(), fld, st, nullptr);
-    emu::launch(152, kThreads, 0, [&] {
-      limit_list_kernel<K>(out, list.data(), &S.ctrl.n_flag, S.t64.data(), S.g, &S.ctrl, 1, yfp, nullptr, nullptr,
-                           S.t32.data());
-    });
+    limit_queued(S, out, list.data(), 1, yfp, nullptr, nullptr, deep);
     ys = out;
   }
   // energy reset (the shadow stays current on the mixed path) and its limiter
@@ -289,17 +299,12 @@ static void run_step(Setup& S, std::vector<double>& y, double dt, const std::vec
   emu::launch(nbr, kThreads, 0, [&] {
     energy_reset_kernel<K, T, 32>(y.data(), tabT, S.t64.data(), S.g, rc, part.data(), list.data(), &S.ctrl, yfp);
   });
-  emu::launch(152, kThreads, 0, [&] {
-    limit_list_kernel<K>(y.data(), list.data(), &S.ctrl.n_flag, S.t64.data(), S.g, &S.ctrl, 0, yfp, nullptr, nullptr,
-                         S.t32.data());
-  });
+  limit_queued(S, y.data(), list.data(), 0, yfp, nullptr, nullptr, deep);
   double diss = 0.0;
   for (unsigned b = 0; b < nbr; ++b) diss += part[b];
   diss *= S.g.dx[0] * S.g.dx[1] * S.g.dx[2];
-  unsigned nb = grid1(nc, kThreads);
-  if (nb > 152u * 8u) nb = 152u * 8u;
   S.ctrl.cfl_max_bits = 0;
-  emu::launch(nb, kThreads, 0, [&] { cfl_kernel<K>(y.data(), S.g, &S.ctrl); });
+  emu::launch(grid1(nc, kThreads), kThreads, 0, [&] { cfl_kernel<K>(y.data(), S.g, &S.ctrl); });
   double smax;
   std::memcpy(&smax, &S.ctrl.cfl_max_bits, 8);
   std::printf("err=%u dissipated=%.17g smax=%.17g\n", S.ctrl.err, diss, smax);

@@ -257,6 +257,7 @@ inline void mma_bf16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[
 
 inline double rsqrt(double x) { return 1.0 / std::sqrt(x); }
 inline float rsqrtf(float x) { return 1.0f / std::sqrt(x); }
+inline float __frcp_rn(float x) { return 1.0f / x; }
 using std::cbrt;
 using std::max;
 using std::min;
