@@ -67,6 +67,16 @@ struct FusedCfg {
   static constexpr size_t smem() { return sizeof(float) * (size_t)TOTAL; }
   static constexpr int MINB = K >= 3 ? 3 : 2;  // CTAs per SM the register budget is sized for
   static constexpr int NFACE = (SX + SY + NC) * Q2;
+  // degree 3: the volume slices and the face points stay loops (unrolled,
+  // the kernel outgrows the instruction cache: ncu showed instruction-fetch
+  // stalls as the largest stall reason; at odd degrees no exact table zero
+  // depends on the slice, so nothing is lost to the rolled loop)
+  static constexpr int SLICE_UNROLL = K >= 3 ? 1 : Q;
+  static constexpr int FACE_UNROLL = K >= 3 ? 1 : 2;
+  // degree 2: the plane's driving field is prefetched to L1 before the
+  // volume slices (3 Q^3 values per cell; at degree 3 the three CTAs per SM
+  // leave too little L1 beside their shared memory)
+  static constexpr bool FIELD_L1 = K <= 2;
 };
 
 // 1D tables of this translation unit's degree in the constant bank:
@@ -138,6 +148,14 @@ __device__ __forceinline__ double f32_to_f64_q(float x) {
   hi = mag < 0x00800000u ? sg : hi;
   lo = mag < 0x00800000u ? 0u : lo;
   return __hiloint2double((int)hi, (int)lo);
+}
+
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+#ifdef __CUDA_ARCH__
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+#else
+  (void)p;
+#endif
 }
 
 __device__ __forceinline__ void prefetch_l2(const void* p) {
@@ -507,7 +525,7 @@ __global__ void __launch_bounds__(FusedCfg<K>::THREADS, FusedCfg<K>::MINB) fused
     // ---------------------------------------------------------------- P2
     if (pz >= 0) {
       const int first = own ? 0 : (SX + SY) * Q2;
-#pragma unroll 2
+#pragma unroll (CF::FACE_UNROLL)
       for (int it = first + tid; it < CF::NFACE; it += CF::THREADS) {
         // item -> direction, face slot and point; o = p SZ + slot is the
         // face point's offset in its direction's trace arrays
@@ -677,9 +695,17 @@ __global__ void __launch_bounds__(FusedCfg<K>::THREADS, FusedCfg<K>::MINB) fused
         for (int l = 0; l < N; ++l, p += rs) prefetch_l2(p);
       }
     }
+    // L1 prefetch of this plane's driving field (3 Q^3 rows of the tile's BY
+    // rows of 8 values), read by the volume slices below
+    if (CF::FIELD_L1 && FORCE && own) {
+      for (int it = tid; it < 3 * Q3 * BY; it += CF::THREADS) {
+        const int row = it / BY, ty = it - row * BY;
+        if (ty < vy) prefetch_l1(a.field + (size_t)row * rs + (size_t)(zoff + (y0 + ty) * g.nx + x0));
+      }
+    }
     // ---------------------------------------------------------------- P6
     if (own) {
-#pragma unroll
+#pragma unroll (CF::SLICE_UNROLL)
       for (int qz = 0; qz < Q; ++qz) {
         // values of variable i at the slice's points
         {

@@ -102,6 +102,12 @@ cudaError_t upload(const double* h64, const float* h32) {
   if (r == cudaSuccess)
     r = cudaFuncSetAttribute(limit_screen_list_kernel<KK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)ListLim<KK>::smem());
+  if (r == cudaSuccess)
+    r = cudaFuncSetAttribute(energy_reset_sf_kernel<KK, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)ResetSF<KK, float>::smem());
+  if (r == cudaSuccess)
+    r = cudaFuncSetAttribute(energy_reset_sf_kernel<KK, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)ResetSF<KK, double>::smem());
   if constexpr (kRegF32) {
     cudaError_t f[4] = {set_f32_smem_fw<MODE_RHS, false>(), set_f32_smem_fw<MODE_RHS, true>(),
                         set_f32_smem_fw<MODE_STAGE, false>(), set_f32_smem_fw<MODE_STAGE, true>()};
@@ -227,24 +233,22 @@ cudaError_t limit(double* y, int8_t* flags, const Geo& g, Ctrl* ctrl, cudaStream
 }
 
 cudaError_t cfl(const double* y, const Geo& g, Ctrl* ctrl, cudaStream_t s) {
-  cfl_kernel<KK><<<grid1(g.nc, kThreads), kThreads, 0, s>>>(y, g, ctrl);
+  cfl_kernel<KK><<<grid1(g.nc, kCflThreads), kCflThreads, 0, s>>>(y, g, ctrl);
   return cudaGetLastError();
 }
-
-constexpr int kResetCells = 32;
 
 template <typename T>
 cudaError_t reset_t(double* y, const Geo& g, double c2g, double inv_rho0, double* part, int* n_part, int* list,
                     Ctrl* ctrl, float* yf, cudaStream_t s) {
-  unsigned nb = grid1(g.nc, kResetCells);
+  using RS = ResetSF<KK, T>;
+  unsigned nb = grid1(g.nc, RS::C);
   *n_part = (int)nb;
   ResetConsts<T> rc;
   rc.c2g = (T)c2g;
   rc.inv_rho0 = (T)inv_rho0;
   rc.gm1 = (T)(g.gamma - 1.0);
   rc.two_thirds = std::fabs(g.gamma - 1.0 - 2.0 / 3.0) < 1e-15 ? 1 : 0;
-  energy_reset_kernel<KK, T, kResetCells><<<nb, kThreads, 0, s>>>(y, tab_ptr<T>(), tab_ptr<double>(), g, rc, part,
-                                                                  list, ctrl, yf);
+  energy_reset_sf_kernel<KK, T><<<nb, RS::THREADS, RS::smem(), s>>>(y, tab_ptr<T>(), g, rc, part, list, ctrl, yf);
   return cudaGetLastError();
 }
 

@@ -1436,12 +1436,16 @@ __global__ void __launch_bounds__(kThreads) limit_kernel(double* __restrict__ y,
 // FP64 s (a few roundings, the pressure's amplified at most 199x by the
 // cancellation, halved by the square root), so the cell holding the
 // block's FP64 maximum is always among the re-evaluated ones. Blocks combine
-// by one atomicMax on the bit pattern of the non-negative double.
+// by one atomicMax on the bit pattern of the non-negative double. Blocks of
+// 1024 cells: a block's re-evaluations (usually the one cell that holds its
+// maximum) occupy the FP64 pipe for a whole warp, so fewer, larger blocks.
+constexpr int kCflThreads = 1024;
+
 template <int K>
-__global__ void __launch_bounds__(kThreads) cfl_kernel(const double* __restrict__ y, Geo g, Ctrl* ctrl) {
+__global__ void __launch_bounds__(kCflThreads) cfl_kernel(const double* __restrict__ y, Geo g, Ctrl* ctrl) {
   constexpr int N = nmodes(K);
   const long long nc = g.nc;
-  const long long c = (long long)blockIdx.x * kThreads + threadIdx.x;
+  const long long c = (long long)blockIdx.x * kCflThreads + threadIdx.x;
   double r = 1.0, m1 = 0.0, m2 = 0.0, m3 = 0.0, E = 0.0;
   float sf = 0.f;
   bool trusted = false;
@@ -1461,8 +1465,8 @@ __global__ void __launch_bounds__(kThreads) cfl_kernel(const double* __restrict_
          (fabsf(m3f) * irf + csf) * f64_to_f32(g.inv_dx[2]);
     trusted = rf >= 1e-30f && rf <= 1e30f && Ef <= 1e30f && kin <= 0.99f * Ef && prf >= 1e-30f && sf <= 3e38f;
   }
-  __shared__ float s_wf[kThreads / 32];
-  __shared__ double s_w[kThreads / 32];
+  __shared__ float s_wf[kCflThreads / 32];
+  __shared__ double s_w[kCflThreads / 32];
   __shared__ unsigned s_err;
   float mf = trusted ? sf : 0.f;
 #pragma unroll
@@ -1472,7 +1476,7 @@ __global__ void __launch_bounds__(kThreads) cfl_kernel(const double* __restrict_
   __syncthreads();
   mf = s_wf[0];
 #pragma unroll
-  for (int w = 1; w < kThreads / 32; ++w) mf = fmaxf(mf, s_wf[w]);
+  for (int w = 1; w < kCflThreads / 32; ++w) mf = fmaxf(mf, s_wf[w]);
   double smax = 0.0;
   unsigned e = 0;
   if (c < nc && (!trusted || sf >= mf * (1.f - 1e-3f))) {
@@ -1492,7 +1496,7 @@ __global__ void __launch_bounds__(kThreads) cfl_kernel(const double* __restrict_
   if (e) atomicOr(&s_err, e);
   __syncthreads();
   if (threadIdx.x < 32) {
-    double v = threadIdx.x < kThreads / 32 ? s_w[threadIdx.x] : 0.0;
+    double v = threadIdx.x < kCflThreads / 32 ? s_w[threadIdx.x] : 0.0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
     if (threadIdx.x == 0) {
@@ -1517,62 +1521,139 @@ struct ResetConsts {
   int two_thirds;        // gamma - 1 within 1e-15 of 2/3
 };
 
-template <int K, typename T, int C>
-__global__ void __launch_bounds__(kThreads) energy_reset_kernel(double* __restrict__ y, const T* __restrict__ tab,
-                                                                const double* __restrict__ tab64, Geo g,
-                                                                ResetConsts<T> rc, double* __restrict__ part,
-                                                                int* __restrict__ list, Ctrl* ctrl,
-                                                                float* __restrict__ yf) {
+// Energy reset with sum-factorised point values (same arithmetic result as a
+// dense evaluation up to rounding order): one thread per (cell, variable)
+// for rho and the momenta loads the variable's N coefficients once and
+// evaluates them at the Q^3 Gauss points along z, then y, then x (the 1D
+// tables of the sum-factorised kernels), writing rows of Q^3 values per cell
+// to shared memory with 16-byte stores; one thread per (cell, point) forms
+// E_q; one thread per (cell, mode) projects E with the weighted table,
+// reading each cell's row of E with 16-byte loads. Rows are padded to a
+// multiple of 16 bytes whose stride spreads the 8 rows of a quarter warp
+// over all 32 banks. The screen sums of rho and the momenta come from the
+// coefficients the value threads hold; those of E from the new modes.
+template <int K, typename T>
+struct ResetSF {
+  static constexpr int C = 32;  // cells per block: one warp per variable
+  static constexpr int THREADS = 4 * C;
+  static constexpr int Q = K + 1, Q3 = Q * Q * Q, N = nmodes(K);
+  static constexpr int V = 16 / (int)sizeof(T);  // elements per 16-byte access
+  // row length: at least Q^3, a multiple of V, and (in 4-byte words) an odd
+  // multiple of 4 modulo 32 apart from row to row
+  static constexpr int ROWW = ((Q3 * (int)sizeof(T) / 4 + 3) / 4) * 4;  // words, multiple of 4
+  static constexpr int ROW = ((ROWW / 4) % 2 == 1 ? ROWW : ROWW + 4) * 4 / (int)sizeof(T);
+  // dynamic shared memory: point values [4][C][ROW] and E [C][ROW]
+  static constexpr size_t smem() { return (size_t)5 * C * ROW * sizeof(T); }
+};
+
+template <int K, typename T>
+__global__ void __launch_bounds__(ResetSF<K, T>::THREADS) energy_reset_sf_kernel(
+    double* __restrict__ y, const T* __restrict__ tab, Geo g, ResetConsts<T> rc, double* __restrict__ part,
+    int* __restrict__ list, Ctrl* ctrl, float* __restrict__ yf) {
+  using RS = ResetSF<K, T>;
   using TB = Tab<K>;
-  constexpr int N = TB::N, Q3 = TB::Q3;
-  __shared__ T sW[4 * N * C];
-  __shared__ T sE[Q3 * C];
-  __shared__ double sEn[N * C];   // new energy modes
-  __shared__ double sM[5 * C];    // means (old energy mean in row 4)
-  static_assert(C == 32, "one warp's worth of cells: the dissipation sum is a warp reduction");
-  __shared__ double sA[5 * C];    // sum_l |w_il| max_S |phi_l| of the reset state
+  constexpr int C = RS::C, Q = RS::Q, Q3 = RS::Q3, N = RS::N, ROW = RS::ROW, V = RS::V;
+  struct alignas(16) Vec {
+    T v[V];
+  };
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sU = reinterpret_cast<T*>(smem_raw);  // [variable][cell][point]
+  T* sE = sU + 4 * C * ROW;                // [cell][point]
+  __shared__ double sEn[N * C];                // new energy modes [mode][cell]
+  __shared__ double sM[5 * C];                 // means (old energy mean in row 4)
+  __shared__ double sA[5 * C];                 // sum_l |w_il| max |phi_l|
   __shared__ int sFin[5 * C];
   const long long nc = g.nc;
   const long long c0 = (long long)blockIdx.x * C;
   const int tid = threadIdx.x;
-  // FP32 path with a valid FP32 shadow: the point values come from it (no
-  // conversions on the FP64 pipe); the means stay FP64
   const bool from_shadow = sizeof(T) == 4 && yf != nullptr;
-  for (int it = tid; it < 4 * N * C; it += kThreads) {
-    const int c = it % C, r = it / C;
+  // ------------------------------------------------ point values of rho, m
+  {
+    const int i = tid / C, c = tid % C;  // warp = variable
     const long long cell = c0 + c;
-    if (r % N == 0) {
-      const double v = cell < nc ? y[(size_t)r * nc + cell] : (r == 0 ? 1.0 : 0.0);
-      if constexpr (sizeof(T) == 4) sW[r * C + c] = f64_to_f32(v);
-      else sW[r * C + c] = v;
-      sM[(r / N) * C + c] = v;
-    } else if (from_shadow) {
-      sW[r * C + c] = cell < nc ? (T)yf[(size_t)r * nc + cell] : T(0);
-    } else {
-      sW[r * C + c] = cell < nc ? (T)y[(size_t)r * nc + cell] : T(0);
+    const bool in = cell < nc;
+    T w[N];
+    double mean = in ? y[(size_t)(i * N) * nc + cell] : (i == 0 ? 1.0 : 0.0);
+    if constexpr (sizeof(T) == 4) w[0] = f64_to_f32(mean);
+    else w[0] = mean;
+#pragma unroll
+    for (int l = 1; l < N; ++l) {
+      if (!in) w[l] = T(0);
+      else if (from_shadow) w[l] = (T)yf[(size_t)(i * N + l) * nc + cell];
+      else w[l] = (T)y[(size_t)(i * N + l) * nc + cell];
+    }
+    sM[i * C + c] = mean;
+    if (tid < C) sM[4 * C + c] = in ? y[(size_t)(4 * N) * nc + cell] : 0.0;
+    // screen sums of this variable from the coefficients held (FP32: of the
+    // rounded coefficients, widened by a relative 1e-5, still an upper bound)
+    {
+      T sa = T(0);
+      bool fin = true;
+#pragma unroll
+      for (int l = 1; l < N; ++l) {
+        T lm;
+        if constexpr (sizeof(T) == 4) lm = g.lim_vol ? c_tab32[TB::LMAXV + l] : c_tab32[TB::LMAX + l];
+        else lm = __ldg(tab + (g.lim_vol ? TB::LMAXV : TB::LMAX) + l);
+        sa += fabs(w[l]) * lm;
+        fin &= isfinite(w[l]);
+      }
+      sA[i * C + c] = in ? (sizeof(T) == 4 ? (double)sa * (1.0 + 1e-5) : (double)sa) : 0.0;
+      sFin[i * C + c] = in ? (int)fin : 1;
+    }
+    // values at q = qx + Q (qy + Q qz): contract z, then y, then x with
+    // Pt_u(x_a) (sfc<T>(u Q + a))
+    T vals[Q3];
+#pragma unroll
+    for (int qz = 0; qz < Q; ++qz) {
+      T A1[(K + 1) * (K + 2) / 2];
+#pragma unroll
+      for (int u = 0, j = 0; u <= K; ++u)
+#pragma unroll
+        for (int v = 0; u + v <= K; ++v, ++j) {
+          T s = T(0);
+#pragma unroll
+          for (int ww = 0; u + v + ww <= K; ++ww) s += w[mode_index(u, v, ww)] * sfc<T>(ww * Q + qz);
+          A1[j] = s;
+        }
+#pragma unroll
+      for (int qy = 0; qy < Q; ++qy) {
+        T A2[K + 1];
+#pragma unroll
+        for (int u = 0, j = 0; u <= K; ++u) {
+          T s = T(0);
+#pragma unroll
+          for (int v = 0; u + v <= K; ++v, ++j) s += A1[j] * sfc<T>(v * Q + qy);
+          A2[u] = s;
+        }
+#pragma unroll
+        for (int qx = 0; qx < Q; ++qx) {
+          T s = T(0);
+#pragma unroll
+          for (int u = 0; u <= K; ++u) s += A2[u] * sfc<T>(u * Q + qx);
+          vals[qx + Q * (qy + Q * qz)] = s;
+        }
+      }
+    }
+    Vec* out = reinterpret_cast<Vec*>(sU + (i * C + c) * ROW);
+#pragma unroll
+    for (int k = 0; k < ROW / V; ++k) {
+      Vec t;
+#pragma unroll
+      for (int e = 0; e < V; ++e) t.v[e] = k * V + e < Q3 ? vals[k * V + e] : T(0);
+      out[k] = t;
     }
   }
-  for (int c = tid; c < C; c += kThreads) {
-    const long long cell = c0 + c;
-    sM[4 * C + c] = cell < nc ? y[(size_t)(4 * N) * nc + cell] : 0.0;
-  }
   __syncthreads();
+  // --------------------------------------------------- E at the points
   const T gm1 = rc.gm1;
   const bool two_thirds = rc.two_thirds != 0;
   const T tc2g = rc.c2g, tir0 = rc.inv_rho0;
-  for (int it = tid; it < Q3 * C; it += kThreads) {
-    const int c = it % C, q = it / C;
-    const T* ph = tab + TB::VPHI + q * N;
-    T U[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      T a = T(0);
-#pragma unroll
-      for (int l = 0; l < N; ++l) a += sW[(i * N + l) * C + c] * __ldg(ph + l);
-      U[i] = a;
-    }
+  for (int it = tid; it < Q3 * C; it += RS::THREADS) {
+    const int c = it / Q3, q = it - c * Q3;  // consecutive threads: consecutive points of a cell
+    const T r = sU[(0 * C + c) * ROW + q];
+    const T m1 = sU[(1 * C + c) * ROW + q], m2 = sU[(2 * C + c) * ROW + q], m3 = sU[(3 * C + c) * ROW + q];
     // gamma = 5/3 (gamma - 1 within 1e-15 of 2/3): x^(2/3) as cbrt(x)^2
-    const T x = U[0] * tir0;
+    const T x = r * tir0;
     T xg;
     if (two_thirds) {
       const T cx = cbrt(x);
@@ -1580,63 +1661,64 @@ __global__ void __launch_bounds__(kThreads) energy_reset_kernel(double* __restri
     } else {
       xg = pow(x, gm1);
     }
-    const T eps = tc2g * xg;
-    sE[q * C + c] = T(0.5) * (U[1] * U[1] + U[2] * U[2] + U[3] * U[3]) / U[0] + U[0] * eps;
+    sE[c * ROW + q] = T(0.5) * (m1 * m1 + m2 * m2 + m3 * m3) / r + r * (tc2g * xg);
   }
   __syncthreads();
-  for (int it = tid; it < N * C; it += kThreads) {
-    const int c = it % C, l = it / C;
+  // --------------------------------------------------- projection of E
+  for (int it = tid; it < N * C; it += RS::THREADS) {
+    const int l = it / C, c = it - l * C;  // a warp: one mode of 32 cells
+    const Vec* row = reinterpret_cast<const Vec*>(sE + c * ROW);
     T acc = T(0);
-    for (int q = 0; q < Q3; ++q) acc += sE[q * C + c] * __ldg(tab + TB::VPHIW + q * N + l);
+#pragma unroll
+    for (int k = 0; k < ROW / V; ++k) {
+      const Vec e = row[k];
+#pragma unroll
+      for (int j = 0; j < V; ++j) {
+        const int q = k * V + j;
+        if (q < Q3) {
+          if constexpr (sizeof(T) == 4) acc += e.v[j] * c_tab32[TB::VPHIW + q * N + l];
+          else acc += e.v[j] * __ldg(tab + TB::VPHIW + q * N + l);
+        }
+      }
+    }
     if constexpr (sizeof(T) == 4) sEn[l * C + c] = f32_to_f64(acc);
     else sEn[l * C + c] = acc;
   }
   __syncthreads();
-  // limiter screen sums of the reset state (density and momentum unchanged),
-  // one (cell, variable) per thread, from the FP64 coefficients
-  for (int it = tid; it < 5 * C; it += kThreads) {
-    const int c = it % C, i = it / C;
-    const long long cell = c0 + c;
-    double sa = 0.0;
-    bool fin = true;
-    if (cell < nc) {
-      if (from_shadow) {
-        // FP32 sums of the rounded coefficients (relative error below 1e-6),
-        // widened by a relative margin of 1e-5: still a sufficient test
-        float sf = 0.f;
-#pragma unroll
-        for (int l = 1; l < N; ++l) {
-          const float v = i < 4 ? (float)sW[(i * N + l) * C + c] : f64_to_f32(sEn[l * C + c]);
-          sf += fabsf(v) * (g.lim_vol ? c_tab32[TB::LMAXV + l] : c_tab32[TB::LMAX + l]);
-          fin &= isfinite(v);
-        }
-        sa = (double)sf * (1.0 + 1e-5);
-      } else {
-        for (int l = 1; l < N; ++l) {
-          const double v = i < 4 ? __ldg(y + (size_t)(i * N + l) * nc + cell) : sEn[l * C + c];
-          sa += fabs(v) * __ldg(tab64 + (g.lim_vol ? TB::LMAXV : TB::LMAX) + l);
-          fin &= isfinite(v);
-        }
-      }
-    }
-    sA[it] = sa;
-    sFin[it] = fin;
-  }
-  __syncthreads();
+  // ------------------------------- screen of the reset state, dissipation
   double diss = 0.0;
   if (tid < C && c0 + tid < nc) {
     const int c = tid;
     const long long cell = c0 + c;
+    double ae = 0.0;
+    bool fin = isfinite(sEn[c]);
+    if constexpr (sizeof(T) == 4) {
+      float sf = 0.f;
+#pragma unroll
+      for (int l = 1; l < N; ++l) {
+        const float v = f64_to_f32(sEn[l * C + c]);
+        sf += fabsf(v) * (g.lim_vol ? c_tab32[TB::LMAXV + l] : c_tab32[TB::LMAX + l]);
+        fin &= isfinite(v);
+      }
+      ae = (double)sf * (1.0 + 1e-5);
+    } else {
+#pragma unroll
+      for (int l = 1; l < N; ++l) {
+        const double v = sEn[l * C + c];
+        ae += fabs(v) * __ldg(tab + (g.lim_vol ? TB::LMAXV : TB::LMAX) + l);
+        fin &= isfinite(v);
+      }
+    }
     const double r = sM[c], m1 = sM[C + c], m2 = sM[2 * C + c], m3 = sM[3 * C + c];
     const double kin = 0.5 * (m1 * m1 + m2 * m2 + m3 * m3) / r;
     diss = (sM[4 * C + c] - kin) - (sEn[c] - kin);
     double m[5] = {r, m1, m2, m3, sEn[c]}, a[5];
-    bool fin = isfinite(sEn[c]);
 #pragma unroll
-    for (int i = 0; i < 5; ++i) {
+    for (int i = 0; i < 4; ++i) {
       a[i] = sA[i * C + c];
       fin &= sFin[i * C + c] != 0;
     }
+    a[4] = ae;
     if (!limiter_screen<K>(m, a, fin, g.gamma, g.eps_rho, g.eps_p)) {
       const unsigned slot = atomicAdd(&ctrl->n_flag, 1u);
       list[slot] = (int)cell;
@@ -1649,8 +1731,8 @@ __global__ void __launch_bounds__(kThreads) energy_reset_kernel(double* __restri
     for (int o = 16; o > 0; o >>= 1) diss += __shfl_xor_sync(0xffffffffu, diss, o);
     if (tid == 0) part[blockIdx.x] = diss;
   }
-  for (int it = tid; it < N * C; it += kThreads) {
-    const int c = it % C, l = it / C;
+  for (int it = tid; it < N * C; it += RS::THREADS) {
+    const int l = it / C, c = it - l * C;
     const long long cell = c0 + c;
     if (cell < nc) {
       y[(size_t)(4 * N + l) * nc + cell] = sEn[l * C + c];

@@ -296,15 +296,15 @@ static void run_step(Setup& S, std::vector<double>& y, double dt, const std::vec
   rc.gm1 = (T)(S.g.gamma - 1.0);
   rc.two_thirds = std::fabs(S.g.gamma - 1.0 - 2.0 / 3.0) < 1e-15 ? 1 : 0;
   const T* tabT = sizeof(T) == 8 ? (const T*)(const void*)S.t64.data() : (const T*)(const void*)S.t32.data();
-  emu::launch(nbr, kThreads, 0, [&] {
-    energy_reset_kernel<K, T, 32>(y.data(), tabT, S.t64.data(), S.g, rc, part.data(), list.data(), &S.ctrl, yfp);
+  emu::launch(nbr, ResetSF<K, T>::THREADS, ResetSF<K, T>::smem(), [&] {
+    energy_reset_sf_kernel<K, T>(y.data(), tabT, S.g, rc, part.data(), list.data(), &S.ctrl, yfp);
   });
   limit_queued(S, y.data(), list.data(), 0, yfp, nullptr, nullptr, deep);
   double diss = 0.0;
   for (unsigned b = 0; b < nbr; ++b) diss += part[b];
   diss *= S.g.dx[0] * S.g.dx[1] * S.g.dx[2];
   S.ctrl.cfl_max_bits = 0;
-  emu::launch(grid1(nc, kThreads), kThreads, 0, [&] { cfl_kernel<K>(y.data(), S.g, &S.ctrl); });
+  emu::launch(grid1(nc, kCflThreads), kCflThreads, 0, [&] { cfl_kernel<K>(y.data(), S.g, &S.ctrl); });
   double smax;
   std::memcpy(&smax, &S.ctrl.cfl_max_bits, 8);
   std::printf("err=%u dissipated=%.17g smax=%.17g\n", S.ctrl.err, diss, smax);

@@ -18,7 +18,7 @@ import synthetic as syn
 
 pytestmark = pytest.mark.gpu
 
-MESH = (37, 33, 29)  # 35,409 cells: 139 blocks of 256, the last one ragged
+MESH = (37, 33, 29)  # 35,409 cells: 35 blocks of 1024, the last one ragged
 
 
 @pytest.fixture(scope="module")
@@ -59,7 +59,7 @@ def base(seed):
     return rng, rho, v, p
 
 
-@pytest.mark.parametrize("where", [0, 35408, 17 * 256 + 3])
+@pytest.mark.parametrize("where", [0, 35408, 17 * 1024 + 3])
 def test_cfl_near_ties(dg, where):
     """Every cell has the same means up to relative 1e-9 perturbations of the
     velocity; the unique FP64 maximum sits in the first, the last (ragged) or
