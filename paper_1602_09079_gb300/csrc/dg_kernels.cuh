@@ -1521,17 +1521,17 @@ struct ResetConsts {
   int two_thirds;        // gamma - 1 within 1e-15 of 2/3
 };
 
-// Energy reset with sum-factorised point values (same arithmetic result as a
-// dense evaluation up to rounding order): one thread per (cell, variable)
+// Energy reset with sum-factorised point values and projection (the same
+// sums as a dense evaluation, reordered): one thread per (cell, variable)
 // for rho and the momenta loads the variable's N coefficients once and
 // evaluates them at the Q^3 Gauss points along z, then y, then x (the 1D
 // tables of the sum-factorised kernels), writing rows of Q^3 values per cell
 // to shared memory with 16-byte stores; one thread per (cell, point) forms
-// E_q; one thread per (cell, mode) projects E with the weighted table,
-// reading each cell's row of E with 16-byte loads. Rows are padded to a
-// multiple of 16 bytes whose stride spreads the 8 rows of a quarter warp
-// over all 32 banks. The screen sums of rho and the momenta come from the
-// coefficients the value threads hold; those of E from the new modes.
+// E_q; the projection of E contracts x first (one (cell, qz, qy) per
+// thread), then y and z per mode. Rows are padded to a multiple of 16 bytes
+// whose stride spreads the 8 rows of a quarter warp over all 32 banks. The
+// screen sums of rho and the momenta come from the coefficients the value
+// threads hold; those of E from the new modes.
 template <int K, typename T>
 struct ResetSF {
   static constexpr int C = 32;  // cells per block: one warp per variable
@@ -1665,22 +1665,47 @@ __global__ void __launch_bounds__(ResetSF<K, T>::THREADS) energy_reset_sf_kernel
   }
   __syncthreads();
   // --------------------------------------------------- projection of E
+  // sum-factorised: G[(qz, qy)][u] = sum_qx E Pt_u(x_qx) w_qx (one (cell,
+  // qz, qy) per thread, into the dead point-value rows), then every mode
+  // (u, v, w) as sum_qz Pt_w w_qz sum_qy Pt_v w_qy G[(qz, qy)][u] (one
+  // (cell, mode) per thread); Pt w from the 1D tables (sfc<T>(KQ + u Q + a))
+  constexpr int KQ = (K + 1) * Q, GROW = Q * Q * (K + 1);
+  T* sG = sU;  // [cell][(qz Q + qy) (K + 1) + u]
+  for (int it = tid; it < Q * Q * C; it += RS::THREADS) {
+    const int c = it / (Q * Q), r = it - c * (Q * Q);  // r = qz Q + qy
+    const T* e = sE + c * ROW + r * Q;
+    T ev[Q];
+#pragma unroll
+    for (int qx = 0; qx < Q; ++qx) ev[qx] = e[qx];
+#pragma unroll
+    for (int u = 0; u <= K; ++u) {
+      T s = T(0);
+#pragma unroll
+      for (int qx = 0; qx < Q; ++qx) s += ev[qx] * sfc<T>(KQ + u * Q + qx);
+      sG[c * GROW + r * (K + 1) + u] = s;
+    }
+  }
+  __syncthreads();
   for (int it = tid; it < N * C; it += RS::THREADS) {
     const int l = it / C, c = it - l * C;  // a warp: one mode of 32 cells
-    const Vec* row = reinterpret_cast<const Vec*>(sE + c * ROW);
+    int u, v, ww;
+    mode_uvw(l, u, v, ww);
+    T pv[Q], pz[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      pv[q] = sfc<T>(KQ + v * Q + q);
+      pz[q] = sfc<T>(KQ + ww * Q + q);
+    }
+    const T* gc = sG + c * GROW + u;
     T acc = T(0);
 #pragma unroll
-    for (int k = 0; k < ROW / V; ++k) {
-      const Vec e = row[k];
+    for (int qz = 0; qz < Q; ++qz) {
+      T h = T(0);
 #pragma unroll
-      for (int j = 0; j < V; ++j) {
-        const int q = k * V + j;
-        if (q < Q3) {
-          if constexpr (sizeof(T) == 4) acc += e.v[j] * c_tab32[TB::VPHIW + q * N + l];
-          else acc += e.v[j] * __ldg(tab + TB::VPHIW + q * N + l);
-        }
-      }
+      for (int qy = 0; qy < Q; ++qy) h += gc[(qz * Q + qy) * (K + 1)] * pv[qy];
+      acc += h * pz[qz];
     }
+    acc *= T(0.125);  // the reference cell's volume 8: w_l = 1/8 sum_q E phi_l w_q
     if constexpr (sizeof(T) == 4) sEn[l * C + c] = f32_to_f64(acc);
     else sEn[l * C + c] = acc;
   }

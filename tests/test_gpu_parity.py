@@ -202,9 +202,11 @@ def test_mixed_step_then_energy_reset_close_to_oracle(dg, order):
         assert st == 0
         assert normwise(s.get_state(), w) <= 1e-6
         # the dissipated energy is a small difference of internal energies
-        # that already carry the mixed step's error: bound it by the
-        # state-level tolerance of the total energy
-        assert abs(d - dref) <= 1e-7 * abs(o.totals(w)[4])
+        # whose new values the mixed path forms in FP32: on a smooth state
+        # every cell rounds alike, so the cells' errors add up coherently;
+        # bound it by the mixed reset's state-level tolerance (1e-6) times
+        # the total energy
+        assert abs(d - dref) <= 1e-6 * abs(o.totals(w)[4])
         w = s.get_state()  # continue both from the GPU state
 
 
