@@ -645,13 +645,27 @@ __global__ void __launch_bounds__(FusedCfg<K>::THREADS, FusedCfg<K>::MINB) fused
       }
       if (own) {
         float Hl[T], Hh[T];
-#pragma unroll (CF::SLICE_UNROLL == 1 ? 1 : 2)
-        for (int d = 0; d < 2; ++d) {
-          const float* base = sm + (d ? CF::YR + fvy * Q2 * SZ : CF::XR + fvx * Q2 * SZ);
-          fz_moments<K>(base + c, SZ, Hl);
-          fz_moments<K>(base + (d ? hy : hx), SZ, Hh);
-          if (d == 0) fz_apply<K, 0>(Hl, Hh, acc);
-          else fz_apply<K, 1>(Hl, Hh, acc);
+        // x and y face pairs: a rolled loop at degree 3 (instruction cache),
+        // written out at degree 2, where the loop form measured 4 % slower
+        // (2.23 vs 2.13 ms per stage at 128^3)
+        if constexpr (CF::SLICE_UNROLL == 1) {
+#pragma unroll 1
+          for (int d = 0; d < 2; ++d) {
+            const float* base = sm + (d ? CF::YR + fvy * Q2 * SZ : CF::XR + fvx * Q2 * SZ);
+            fz_moments<K>(base + c, SZ, Hl);
+            fz_moments<K>(base + (d ? hy : hx), SZ, Hh);
+            if (d == 0) fz_apply<K, 0>(Hl, Hh, acc);
+            else fz_apply<K, 1>(Hl, Hh, acc);
+            if (i == 0) accm += f32_to_f64_q(Hl[0]) - f32_to_f64_q(Hh[0]);
+          }
+        } else {
+          fz_moments<K>(sm + CF::XR + fvx * Q2 * SZ + c, SZ, Hl);
+          fz_moments<K>(sm + CF::XR + fvx * Q2 * SZ + hx, SZ, Hh);
+          fz_apply<K, 0>(Hl, Hh, acc);
+          if (i == 0) accm += f32_to_f64_q(Hl[0]) - f32_to_f64_q(Hh[0]);
+          fz_moments<K>(sm + CF::YR + fvy * Q2 * SZ + c, SZ, Hl);
+          fz_moments<K>(sm + CF::YR + fvy * Q2 * SZ + hy, SZ, Hh);
+          fz_apply<K, 1>(Hl, Hh, acc);
           if (i == 0) accm += f32_to_f64_q(Hl[0]) - f32_to_f64_q(Hh[0]);
         }
       }
