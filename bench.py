@@ -384,9 +384,10 @@ def run_ours(args):
     fp32_probe = dgm.dg_probe_fma_peak(False)
 
     def kernel_roofline(prec_name, tsize):
-        """Roofline of one RK stage: the stage kernels' time per
-        stage (the fused kernel on the mixed path at degree 2; face and volume
-        kernels otherwise) against the algorithmic bytes and flops of a stage
+        """Roofline of one RK stage: the stage kernels' time per stage (the
+        fused kernel on the mixed path at degrees 2-3; face and volume kernels
+        otherwise) against the method's algorithmic bytes (read y_s and y_0,
+        write y_{s+1} in FP64) and sum-factorised flops of a stage
         (roofline.stage_roofline); traffic = the ncu DRAM bytes of the timed
         kernel per launch, with its ratio to the algorithmic bytes."""
         kst = results[prec_name]["ktimes"]

@@ -36,7 +36,7 @@ def test_fp64_step_bytes_by_hand():
 
 
 def test_stage_algorithmic_counts_by_hand():
-    """read y_s, y_0 (stages 2-3), write y_{s+1} in FP64, i.e.
+    """Algorithmic bytes of a stage: read y_s, y_0 (stages 2-3), write y_{s+1} in FP64, i.e.
     8/3 x 5 N x 8 bytes per cell per stage; flops: the sum-factorised volume
     integral with the source and three owned faces."""
     for k in (1, 2, 3):
