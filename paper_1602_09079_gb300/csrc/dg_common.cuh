@@ -137,7 +137,7 @@ __device__ __forceinline__ void euler_flux(int d, const T* U, const T* v, T p, T
 }
 
 // HLLC numerical flux across a face with normal +e_d, left = lower cell
-// (Sect. 2.3, "approximative HLLC Riemann solver"): Einfeldt wave-speed
+// (Sect. 2.3, the approximate HLLC Riemann solver): Einfeldt wave-speed
 // estimates from Roe averages, middle wave and star states from the
 // Rankine-Hugoniot conditions across the three waves (Toro's formulation).
 // ------------------------------------------- IEEE 754 conversions
