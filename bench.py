@@ -399,7 +399,7 @@ def run_ours(args):
         e["peak_source"] = rl.PEAK_SOURCE
         fused = tsize == 4 and nface == 0
         if fused:
-            kname = f"fused_f32_kernel<{k}, true, 0>"
+            kname = f"fused_f32_kernel<{k}, true, {1 if args.flux == 'exact' else 0}>"
             e["kernel"] = kname + " (stage, forcing; face fluxes, volume integral and stage update in one launch)"
             e["impl_bytes_per_launch"] = rl.fused_impl_bytes(k, True) * nc
         else:
@@ -410,7 +410,9 @@ def run_ours(args):
             e["kernel"] = kname + " (stage, forcing) + its face kernel"
             e["impl_bytes_per_launch"] = (rl.volume_bytes(k, tsize, True, shadow=tsize == 4)
                                           + rl.face_bytes(k, tsize)) * nc
-        tr = ncu_traffic().get(kname)
+        # the captured FP64 traffic is that of the HLLC face kernel: no entry
+        # for the exact-flux path
+        tr = None if (args.flux == "exact" and not fused) else ncu_traffic().get(kname)
         e["traffic"] = None
         if tr and not tr.get("stale"):
             e["traffic"] = tr["dram_bytes_per_cell"] * nc
@@ -464,7 +466,7 @@ def run_ours(args):
             "speedup_mixed_over_fp64": value / value64,
             "mixed_vs_fp64_error": {"steps": err_steps, "dt": dt_fix,
                                     "l2_rel_per_var": l2, "max_coef_rel_per_var": mx},
-            "e2e": {"value": e2e_dof / e2e_s, "unit": "DOF-updates/s",
+            "e2e": {"value": (e2e_dof / e2e_s) if args.e2e_steps > 0 else None, "unit": "DOF-updates/s",
                     "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes,
                     "note": "dg_set_state from pinned host + step + dg_get_state to pinned host, per step"},
             "gpu_launches": launches,
