@@ -246,8 +246,9 @@ int dg_check(dg_ctx* ctx);
  * events recorded on the bound stream (adds two event records per launch). */
 int dg_set_timing(dg_ctx* ctx, int on);
 
-/* Per class: launches since the last call (always counted) and, if timing
- * was on, their summed device time in ms (0 otherwise). Synchronises the
+/* Per class: kernel launches since the last call (always counted; the
+ * queued limiter's two passes count as two) and, if timing was on, their
+ * summed device time in ms (0 otherwise). Synchronises the
  * stream; resets the counters. Arrays of DG_KCLASS_COUNT entries, either may
  * be NULL. */
 int dg_kernel_stats(dg_ctx* ctx, int64_t* launches, double* ms);

@@ -458,10 +458,11 @@ cudaEvent_t take_event(dg_ctx* c) {
   return e;
 }
 
-// Every kernel launch of a context goes through here: counted per class and,
-// with timing on, bracketed by events on the bound stream.
+// Every kernel launch of a context goes through here: counted per class (nk
+// = the number of kernels f launches) and, with timing on, bracketed by
+// events on the bound stream.
 template <class F>
-int launch(dg_ctx* c, int cls, F&& f) {
+int launch(dg_ctx* c, int cls, F&& f, int nk = 1) {
   cudaEvent_t a = nullptr, b = nullptr;
   if (c->timing) {
     a = take_event(c);
@@ -470,7 +471,7 @@ int launch(dg_ctx* c, int cls, F&& f) {
     DG_CUDA(cudaEventRecord(a, c->stream));
   }
   cudaError_t e = f();
-  c->launches[cls] += 1;
+  c->launches[cls] += nk;
   if (c->timing) {
     DG_CUDA(cudaEventRecord(b, c->stream));
     c->pending.push_back({cls, a, b});
@@ -563,12 +564,12 @@ int fused_step(dg_ctx* c, double dt, bool force) {
       DG_TRY(launch(c, KC_LIMIT, [&] {
         return c->fn.limit_list(out, c->list2, &c->ctrl->n_gate, c->geo, c->ctrl, 0, yf, y0, dinc, c->list,
                                 c->stream);
-      }));
+      }, 2));
     } else {
       DG_TRY(launch(c, KC_LIMIT, [&] {
         return c->fn.limit_list(out, c->list, &c->ctrl->n_flag, c->geo, c->ctrl, 1, yf, y0, dinc, c->list2,
                                 c->stream);
-      }));
+      }, 2));
     }
     ys = out;
   }
@@ -843,12 +844,12 @@ int dg_step(dg_ctx* c, double dt) {
       DG_TRY(launch(c, KC_LIMIT, [&] {
         return c->fn.limit_list(out, c->list2, &c->ctrl->n_gate, c->geo, c->ctrl, 0, yf, nullptr, nullptr, c->list,
                                 c->stream);
-      }));
+      }, 2));
     } else {
       DG_TRY(launch(c, KC_LIMIT, [&] {
         return c->fn.limit_list(out, c->list, &c->ctrl->n_flag, c->geo, c->ctrl, 1, yf, nullptr, nullptr, c->list2,
                                 c->stream);
-      }));
+      }, 2));
     }
     ys = out;
   }
@@ -968,7 +969,7 @@ int dg_energy_reset(dg_ctx* c, double c_iso, double rho0, double* dissipated) {
   DG_TRY(launch(c, KC_RESET, [&] {
     return c->fn.limit_list(c->y, c->list, &c->ctrl->n_flag, c->geo, c->ctrl, 0, yf, nullptr, nullptr, c->list2,
                                 c->stream);
-  }));
+  }, 2));
   c->limited = true;
   if (dissipated) {
     const double vol = c->geo.dx[0] * c->geo.dx[1] * c->geo.dx[2];
